@@ -1,0 +1,226 @@
+"""Python binding of the cc C ABI (include/cc.h): argument marshalling only.
+
+Every step of the pair counting runs in the CUDA kernels of libcc.so; this module only
+turns torch tensors into device pointers and streams into handles. There is no CPU
+fallback: if libcc.so is missing or fails to load, every call raises.
+
+The functions named cc_* mirror the C entry points one to one. The convenience helpers
+(count_pairs, interaction_sum, count_pairs_batched, Plan, Server) take torch CUDA tensors
+and return torch tensors that live on the device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcc.so")
+
+CC_OK = 0
+CC_ERR_INVALID_ARG = 1
+CC_ERR_RANGE = 2
+CC_ERR_NOMEM = 3
+CC_ERR_CUDA = 4
+CC_ERR_TIMEOUT = 5
+CC_ERR_BUSY = 6
+CC_ERR_NOT_FOUND = 7
+CC_I32 = 0
+CC_F32 = 1
+CC_OP_COUNT = 0
+CC_OP_SUM = 1
+CC_COUNT_INVALID = 0xFFFFFFFFFFFFFFFF
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS_NAMES = {0: "CC_OK", 1: "CC_ERR_INVALID_ARG", 2: "CC_ERR_RANGE", 3: "CC_ERR_NOMEM",
+                 4: "CC_ERR_CUDA", 5: "CC_ERR_TIMEOUT", 6: "CC_ERR_BUSY", 7: "CC_ERR_NOT_FOUND"}
+
+
+class cc_points(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("z", ctypes.c_void_p), ("r", ctypes.c_void_p)]
+
+
+class cc_result(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("set_id", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("count", ctypes.c_ulonglong), ("sum", ctypes.c_float), ("pad2", ctypes.c_float),
+                ("t_arrive_s", ctypes.c_double), ("t_done_s", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_VP = ctypes.c_void_p
+_PTS = ctypes.POINTER(cc_points)
+_SIGS = {
+    "cc_count_pairs": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
+    "cc_interaction_sum": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
+    "cc_validate_points": ([_PTS, ctypes.c_int64, _VP], ctypes.c_int),
+    "cc_reserve": ([ctypes.c_int64, _VP], ctypes.c_int),
+    "cc_release": ([_VP], ctypes.c_int),
+    "cc_stream_status": ([_VP], ctypes.c_int),
+    "cc_plan_create": ([ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
+    "cc_plan_destroy": ([_VP], None),
+    "cc_count_pairs_batched": ([_VP, _PTS, _VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
+    "cc_plan_last_items": ([_VP, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cc_server_create": ([ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int32], ctypes.c_int),
+    "cc_server_register_set": ([_VP, _PTS, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cc_server_unregister_set": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "cc_server_submit": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64], ctypes.c_int),
+    "cc_server_poll": ([_VP, ctypes.POINTER(cc_result), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cc_server_drain": ([_VP, ctypes.c_double], ctypes.c_int),
+    "cc_server_stats": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cc_server_destroy": ([_VP], None),
+    "cc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "cc_last_error": ([], ctypes.c_char_p),
+    "cc_version": ([], ctypes.c_char_p),
+    "cc_set_wait_limit_ns": ([ctypes.c_uint64], None),
+    "cc_debug_stall_copies": ([ctypes.c_int], None),
+}
+
+
+def lib():
+    """The loaded libcc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libcc.so not built ({LIB_PATH}); run __graft_entry__.build() "
+                                   "or python paper_1901_11204_gb300/builder.py")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (argt, rest) in _SIGS.items():
+                if not hasattr(L, name):
+                    continue
+                f = getattr(L, name)
+                f.argtypes = argt
+                f.restype = rest
+            _lib = L
+        return _lib
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from . import builder
+    return builder.build(force=force, verbose=verbose)
+
+
+def _check(status: int):
+    if status != CC_OK:
+        raise CCError(status, lib().cc_last_error().decode())
+
+
+# ---- thin 1:1 wrappers over the C ABI (raw pointers / handles) -------------------------
+
+def cc_count_pairs(points: cc_points, n: int, r2: int, d_count: int, stream: int) -> int:
+    return lib().cc_count_pairs(ctypes.byref(points), n, r2, d_count, stream)
+
+
+def cc_interaction_sum(points: cc_points, n: int, r2: int, d_sum: int, d_count: int, stream: int) -> int:
+    return lib().cc_interaction_sum(ctypes.byref(points), n, r2, d_sum, d_count, stream)
+
+
+def cc_validate_points(points: cc_points, n: int, stream: int) -> int:
+    return lib().cc_validate_points(ctypes.byref(points), n, stream)
+
+
+def cc_count_pairs_batched(plan: int, points: cc_points, d_offsets: int, n_sets: int, r2: int,
+                           d_counts: int, d_sums: int, stream: int) -> int:
+    return lib().cc_count_pairs_batched(plan, ctypes.byref(points), d_offsets, n_sets, r2,
+                                        d_counts, d_sums, stream)
+
+
+def cc_stream_status(stream: int) -> int:
+    return lib().cc_stream_status(stream)
+
+
+# ---- torch helpers ---------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def make_points(x, y, z, r=None) -> cc_points:
+    """cc_points over device tensors (int32 x/y/z, or float32 x/y/z/r)."""
+    torch = _torch()
+    for t in (x, y, z) + ((r,) if r is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("coordinates must be contiguous CUDA tensors")
+    if x.dtype == torch.int32:
+        return cc_points(CC_I32, x.data_ptr(), y.data_ptr(), z.data_ptr(), None)
+    if x.dtype == torch.float32:
+        if r is None or r.dtype != torch.float32:
+            raise ValueError("FP32 spheres need float32 radii")
+        return cc_points(CC_F32, x.data_ptr(), y.data_ptr(), z.data_ptr(), r.data_ptr())
+    raise ValueError(f"unsupported dtype {x.dtype}")
+
+
+def count_pairs(x, y, z, r2: int = 0, r=None, out=None, stream=None):
+    """Exact colliding-pair count of one set; returns a 1-element uint64 (int64 view)
+    device tensor. Asynchronous on `stream` (default: torch's current stream)."""
+    torch = _torch()
+    pts = make_points(x, y, z, r)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=x.device)
+    _check(cc_count_pairs(pts, x.numel(), int(r2), out.data_ptr(), _stream_handle(stream)))
+    return out
+
+
+def interaction_sum(x, y, z, r2: int = 0, r=None, out_sum=None, out_count=None, stream=None):
+    """(sum, count) device tensors: FP32 sum of 1/max(d, 1e-6) over colliding pairs and
+    their number."""
+    torch = _torch()
+    pts = make_points(x, y, z, r)
+    if out_sum is None:
+        out_sum = torch.empty(1, dtype=torch.float32, device=x.device)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=x.device)
+    _check(cc_interaction_sum(pts, x.numel(), int(r2), out_sum.data_ptr(), out_count.data_ptr(),
+                              _stream_handle(stream)))
+    return out_sum, out_count
+
+
+def validate_points(x, y, z, r=None, stream=None) -> int:
+    """Synchronous range check; returns the cc_status (CC_OK or CC_ERR_RANGE)."""
+    pts = make_points(x, y, z, r)
+    return cc_validate_points(pts, x.numel(), _stream_handle(stream))
+
+
+def stream_status(stream=None) -> int:
+    return cc_stream_status(_stream_handle(stream))
+
+
+def reserve(max_n: int, stream=None):
+    _check(lib().cc_reserve(int(max_n), _stream_handle(stream)))
+
+
+def set_wait_limit_ns(ns: int):
+    lib().cc_set_wait_limit_ns(int(ns))
+
+
+def debug_stall_copies(on: bool):
+    lib().cc_debug_stall_copies(1 if on else 0)
+
+
+def version() -> str:
+    return lib().cc_version().decode()
+
+
+def as_u64(t) -> int:
+    """Python int of a 1-element int64 tensor holding an unsigned 64-bit count."""
+    v = int(t.item())
+    return v & 0xFFFFFFFFFFFFFFFF

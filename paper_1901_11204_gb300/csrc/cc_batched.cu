@@ -1,0 +1,637 @@
+// Batched sets: many independent sets (the pruned cells a broad phase emits) in one
+// persistent launch with a device-built work queue, replayed as one CUDA graph.
+//
+// Each set runs the proposed algorithm of Section 4 on its own: object i of a set of n
+// evaluates (i+s) mod n for s = 1..(n-1)/2, plus s = n/2 for i < n/2 when n is even.
+// Because every object does the same number of steps, a set splits into equal work
+// items along both axes: an item is (set, block of 32*R consecutive objects, chunk of
+// SC consecutive steps). R and SC come from a per-size-band table (the autotuner writes
+// it); tile choice is a pure function of (n, table), so results are reproducible.
+//
+// Graph (all kernels read the call's parameters from a device descriptor, so the
+// captured graph is replayed unchanged for every call):
+//   k_b_prepare  one warp per set: set descriptor, per-set range check, item count
+//   k_b_scan1/2  exclusive prefix sum of the item counts (two levels)
+//   k_b_emit     one warp per set: writes its items to the queue
+//   k_b_main     persistent warps pull items with an atomic cursor; per-item partials
+//   k_b_finish   one warp per set: fixed-order sum of its items' partials
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cc_internal.cuh"
+
+namespace cc {
+
+constexpr int kMaxBands = 8;
+constexpr int kScanBlock = 1024;
+
+struct Band {
+    int64_t n_max;   // sets with n <= n_max (and above the previous band) use this band
+    int32_t r;       // objects per lane (1, 2, 4 or 8)
+    int32_t sc;      // steps per item; 0 = grow with n (max(4096, n/8))
+};
+
+struct BandTable {
+    int32_t count;
+    int32_t pad;
+    Band band[kMaxBands];
+};
+
+// One set of the batch.
+struct SetDesc {
+    const void *x, *y, *z;
+    const float *r;
+    int64_t n;
+    int32_t dtype;
+    uint32_t r2;
+};
+
+// Per-call parameters (device-resident, rewritten before each graph replay).
+struct BatchParams {
+    cc_points pts;                 // shared coordinate arrays (offsets mode)
+    const int64_t *offsets;        // device offsets, or NULL when sets[] is pre-filled
+    int32_t n_sets;
+    uint32_t r2;
+    int32_t want_sum;
+    int32_t pad;
+    unsigned long long *d_counts;
+    float *d_sums;
+};
+
+// Device-side state of a plan.
+struct BatchState {
+    int64_t total_items;
+    int64_t cursor;
+    uint32_t status;
+    uint32_t pad;
+};
+
+struct Item {
+    int32_t set;
+    int32_t local;
+};
+
+enum : uint32_t { SET_OK = 0, SET_BAD_RANGE = 1, SET_BAD_OFFSETS = 2, SET_OVERFLOW = 4 };
+
+__device__ __forceinline__ const Band &band_of(const BandTable &bt, int64_t n) {
+    for (int b = 0; b < bt.count - 1; ++b)
+        if (n <= bt.band[b].n_max) return bt.band[b];
+    return bt.band[bt.count - 1];
+}
+
+__host__ __device__ __forceinline__ int64_t steps_of(int64_t n) {
+    return n < 2 ? 0 : (n - 1) / 2 + ((n & 1) == 0 ? 1 : 0);
+}
+
+__host__ __device__ __forceinline__ int64_t sc_of(const Band &b, int64_t n) {
+    if (b.sc > 0) return b.sc;
+    int64_t v = n / 8;
+    return v > 4096 ? v : 4096;
+}
+
+__host__ __device__ __forceinline__ int64_t items_of(const Band &b, int64_t n) {
+    if (n < 2) return 0;
+    const int64_t per = 32 * static_cast<int64_t>(b.r);
+    const int64_t sc = sc_of(b, n);
+    return ((n + per - 1) / per) * ((steps_of(n) + sc - 1) / sc);
+}
+
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, const BandTable *bt,
+                            int32_t *cnt, uint32_t *flags, BatchState *st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t S = P->n_sets;
+    if (warp == 0 && lane == 0) {
+        st->cursor = 0;
+        st->status = 0;
+    }
+    for (int64_t k = warp; k < S; k += nwarps) {
+        SetDesc d;
+        uint32_t flag = SET_OK;
+        if (P->offsets) {
+            const int64_t a = P->offsets[k], b = P->offsets[k + 1];
+            const size_t es = 4;
+            d.x = static_cast<const char *>(P->pts.x) + a * es;
+            d.y = static_cast<const char *>(P->pts.y) + a * es;
+            d.z = static_cast<const char *>(P->pts.z) + a * es;
+            d.r = P->pts.dtype == CC_F32 ? P->pts.r + a : nullptr;
+            d.n = b - a;
+            d.dtype = P->pts.dtype;
+            d.r2 = P->r2;
+            if (a < 0 || b < a) {
+                flag = SET_BAD_OFFSETS;
+                d.n = 0;
+            }
+            if (lane == 0) sets[k] = d;
+        } else {
+            d = sets[k];
+        }
+        // integer range precondition, per set (span <= 32767 on every axis)
+        if (flag == SET_OK && d.dtype == CC_I32 && d.n >= 2) {
+            uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0, 0, 0};
+            const int32_t *c[3] = {static_cast<const int32_t *>(d.x), static_cast<const int32_t *>(d.y),
+                                   static_cast<const int32_t *>(d.z)};
+            for (int64_t i = lane; i < d.n; i += 32)
+                for (int a = 0; a < 3; ++a) {
+                    const uint32_t u = ord_enc(c[a][i]);
+                    mn[a] = min(mn[a], u);
+                    mx[a] = max(mx[a], u);
+                }
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = __reduce_min_sync(0xFFFFFFFFu, mn[a]);
+                mx[a] = __reduce_max_sync(0xFFFFFFFFu, mx[a]);
+                if (static_cast<int64_t>(ord_dec(mx[a])) - ord_dec(mn[a]) > WIDE_MAX_SPAN)
+                    flag = SET_BAD_RANGE;
+            }
+        }
+        if (lane == 0) {
+            const int64_t it = flag == SET_OK ? items_of(band_of(*bt, d.n), d.n) : 0;
+            cnt[k] = static_cast<int32_t>(min<int64_t>(it, 0x7FFFFFFF));
+            flags[k] = flag;
+        }
+    }
+}
+
+// Block-level exclusive scan of cnt (kScanBlock per block); block totals to bsum.
+__global__ void k_b_scan1(const BatchParams *__restrict__ P, const int32_t *cnt, int64_t *start,
+                          int64_t *bsum) {
+    __shared__ int64_t warp_tot[kScanBlock / 32];
+    const int32_t S = P->n_sets;
+    const int64_t k = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    if (blockIdx.x * (int64_t)kScanBlock >= S) {
+        if (threadIdx.x == 0) bsum[blockIdx.x] = 0;
+        return;
+    }
+    int64_t v = k < S ? cnt[k] : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < kScanBlock / 32 ? warp_tot[lane] : 0;
+        int64_t ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xFFFFFFFFu, ti, o);
+            if (lane >= o) ti += u;
+        }
+        if (lane < kScanBlock / 32) warp_tot[lane] = ti - t;   // exclusive warp offsets
+        if (lane == kScanBlock / 32 - 1) bsum[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    if (k < S) start[k] = incl - v + warp_tot[w];
+}
+
+// Exclusive scan of the block totals (one block); writes the grand total.
+__global__ void k_b_scan2(int64_t *bsum, int32_t nblocks, BatchState *st, int64_t capacity) {
+    __shared__ int64_t buf[kScanBlock];
+    const int t = threadIdx.x;
+    buf[t] = t < nblocks ? bsum[t] : 0;
+    __syncthreads();
+    for (int o = 1; o < kScanBlock; o <<= 1) {
+        int64_t u = t >= o ? buf[t - o] : 0;
+        __syncthreads();
+        buf[t] += u;
+        __syncthreads();
+    }
+    if (t < nblocks) bsum[t] = buf[t] - (t < nblocks ? bsum[t] : 0);
+    if (t == kScanBlock - 1) {
+        st->total_items = buf[t];
+        if (buf[t] > capacity) {
+            st->status |= SET_OVERFLOW;
+            st->total_items = 0;
+        }
+    }
+}
+
+__global__ void k_b_emit(const BatchParams *__restrict__ P, const int32_t *cnt, const int64_t *start,
+                         const int64_t *bsum, Item *items, const BatchState *st) {
+    if (st->status & SET_OVERFLOW) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = warp; k < P->n_sets; k += nwarps) {
+        const int64_t s0 = start[k] + bsum[k / kScanBlock];
+        const int32_t c = cnt[k];
+        for (int32_t t = lane; t < c; t += 32) items[s0 + t] = Item{static_cast<int32_t>(k), t};
+    }
+}
+
+// ---- the per-item pair loop -------------------------------------------------------------
+
+template <int R>
+__device__ void run_item(const SetDesc &d, const Band &b, int32_t local, bool want_sum,
+                         unsigned long long &cnt_out, double &sum_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = d.n;
+    const int64_t h = (n - 1) / 2;
+    const int64_t steps = steps_of(n);
+    const int64_t per = 32 * R;
+    const int64_t nbi = (n + per - 1) / per;
+    const int64_t sc = sc_of(b, n);
+    const int64_t ib = local % nbi;
+    const int64_t ch = local / nbi;
+    const int64_t s0 = ch * sc + 1;
+    const int64_t s1 = min(s0 + sc, steps + 1);
+    const int64_t half = n / 2;
+
+    int64_t iv[R];
+    bool ok[R];
+    bool first_half[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = ib * per + lane + 32 * r;
+        ok[r] = i < n;
+        iv[r] = ok[r] ? i : n - 1;
+        first_half[r] = iv[r] < half;
+    }
+    uint32_t cnt = 0;
+    double sum = 0.0;
+    if (d.dtype == CC_I32) {
+        const int32_t *X = static_cast<const int32_t *>(d.x);
+        const int32_t *Y = static_cast<const int32_t *>(d.y);
+        const int32_t *Z = static_cast<const int32_t *>(d.z);
+        int32_t xi[R], yi[R], zi[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            xi[r] = X[iv[r]];
+            yi[r] = Y[iv[r]];
+            zi[r] = Z[iv[r]];
+        }
+        for (int64_t s = s0; s < s1; ++s) {
+            const bool last_even = s > h;   // s == n/2 of an even set
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int64_t j = iv[r] + s;
+                if (j >= n) j -= n;
+                const int32_t dx = xi[r] - __ldg(X + j);
+                const int32_t dy = yi[r] - __ldg(Y + j);
+                const int32_t dz = zi[r] - __ldg(Z + j);
+                const uint32_t d2 = static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy) +
+                                    static_cast<uint32_t>(dz * dz);
+                const bool hit = d2 <= d.r2 && ok[r] && (!last_even || first_half[r]);
+                cnt += hit ? 1u : 0u;
+                if (want_sum && hit)
+                    sum += static_cast<double>(__fdiv_rn(1.0f, fmaxf(__fsqrt_rn(static_cast<float>(d2)), 1e-6f)));
+            }
+        }
+    } else {
+        const float *X = static_cast<const float *>(d.x);
+        const float *Y = static_cast<const float *>(d.y);
+        const float *Z = static_cast<const float *>(d.z);
+        const float *Rr = d.r;
+        float xi[R], yi[R], zi[R], ri[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            xi[r] = X[iv[r]];
+            yi[r] = Y[iv[r]];
+            zi[r] = Z[iv[r]];
+            ri[r] = Rr[iv[r]];
+        }
+        for (int64_t s = s0; s < s1; ++s) {
+            const bool last_even = s > h;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int64_t j = iv[r] + s;
+                if (j >= n) j -= n;
+                const float dx = __fsub_rn(xi[r], __ldg(X + j));
+                const float dy = __fsub_rn(yi[r], __ldg(Y + j));
+                const float dz = __fsub_rn(zi[r], __ldg(Z + j));
+                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                const float sr = __fadd_rn(ri[r], __ldg(Rr + j));
+                const bool hit = d2 <= __fmul_rn(sr, sr) && ok[r] && (!last_even || first_half[r]);
+                cnt += hit ? 1u : 0u;
+                if (want_sum && hit)
+                    sum += static_cast<double>(__fdiv_rn(1.0f, fmaxf(__fsqrt_rn(d2), 1e-6f)));
+            }
+        }
+    }
+    // warp reduction (fixed order)
+    unsigned long long c64 = cnt;
+    for (int o = 16; o > 0; o >>= 1) {
+        c64 += __shfl_down_sync(0xFFFFFFFFu, c64, o);
+        if (want_sum) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    }
+    cnt_out = c64;
+    sum_out = sum;
+}
+
+__global__ void __launch_bounds__(256) k_b_main(const BatchParams *__restrict__ P, const SetDesc *sets,
+                                                const BandTable *bt, const Item *items, BatchState *st,
+                                                unsigned long long *pcnt, double *psum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = st->total_items;
+    const bool want_sum = P->want_sum != 0;
+    for (;;) {
+        int64_t it = 0;
+        if (lane == 0) it = static_cast<int64_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&st->cursor), 1ull));
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= total) break;
+        const Item item = items[it];
+        const SetDesc d = sets[item.set];
+        const Band b = band_of(*bt, d.n);
+        unsigned long long c = 0;
+        double s = 0.0;
+        switch (b.r) {
+            case 1: run_item<1>(d, b, item.local, want_sum, c, s); break;
+            case 2: run_item<2>(d, b, item.local, want_sum, c, s); break;
+            case 4: run_item<4>(d, b, item.local, want_sum, c, s); break;
+            default: run_item<8>(d, b, item.local, want_sum, c, s); break;
+        }
+        if (lane == 0) {
+            pcnt[it] = c;
+            if (want_sum) psum[it] = s;
+        }
+    }
+}
+
+__global__ void k_b_finish(const BatchParams *__restrict__ P, const int32_t *cnt, const int64_t *start,
+                           const int64_t *bsum, const uint32_t *flags, const BatchState *st,
+                           const unsigned long long *pcnt, const double *psum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool overflow = (st->status & SET_OVERFLOW) != 0;
+    const bool want_sum = P->want_sum != 0;
+    for (int64_t k = warp; k < P->n_sets; k += nwarps) {
+        const int64_t s0 = start[k] + bsum[k / kScanBlock];
+        const int32_t c = cnt[k];
+        unsigned long long tc = 0;
+        double ts = 0.0;
+        if (!overflow) {
+            for (int32_t t = lane; t < c; t += 32) {
+                tc += pcnt[s0 + t];
+                if (want_sum) ts += psum[s0 + t];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                tc += __shfl_down_sync(0xFFFFFFFFu, tc, o);
+                if (want_sum) ts += __shfl_down_sync(0xFFFFFFFFu, ts, o);
+            }
+        }
+        if (lane == 0) {
+            const bool bad = overflow || flags[k] != SET_OK;
+            P->d_counts[k] = bad ? CC_COUNT_INVALID : tc;
+            if (want_sum && P->d_sums) P->d_sums[k] = bad ? __int_as_float(0x7fc00000) : static_cast<float>(ts);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side: plan, band table, graph
+// ---------------------------------------------------------------------------------------
+
+static BandTable default_bands() {
+    BandTable t{};
+    t.count = 5;
+    t.band[0] = Band{64, 1, 64};
+    t.band[1] = Band{512, 2, 256};
+    t.band[2] = Band{8192, 4, 1024};
+    t.band[3] = Band{65536, 8, 4096};
+    t.band[4] = Band{INT64_MAX, 8, 0};
+    return t;
+}
+
+// Minimal parser for {"bands": [{"n_max": N, "r": R, "sc": S}, ...]} (n_max -1 = no limit).
+static bool parse_bands(const char *json, BandTable &out, std::string &err) {
+    BandTable t{};
+    const char *p = strstr(json, "\"bands\"");
+    if (!p) { err = "missing \"bands\""; return false; }
+    p = strchr(p, '[');
+    if (!p) { err = "missing band list"; return false; }
+    ++p;
+    while (true) {
+        const char *ob = strchr(p, '{');
+        const char *end = strchr(p, ']');
+        if (!ob || (end && end < ob)) break;
+        const char *cb = strchr(ob, '}');
+        if (!cb) { err = "unterminated band"; return false; }
+        std::string obj(ob, cb - ob);
+        auto field = [&](const char *name, long long &v) {
+            size_t q = obj.find(std::string("\"") + name + "\"");
+            if (q == std::string::npos) return false;
+            q = obj.find(':', q);
+            if (q == std::string::npos) return false;
+            v = strtoll(obj.c_str() + q + 1, nullptr, 10);
+            return true;
+        };
+        long long nmax = 0, r = 0, sc = 0;
+        if (!field("n_max", nmax) || !field("r", r) || !field("sc", sc)) { err = "band needs n_max, r, sc"; return false; }
+        if (t.count >= kMaxBands) { err = "too many bands"; return false; }
+        if (!(r == 1 || r == 2 || r == 4 || r == 8) || sc < 0) { err = "r must be 1,2,4,8 and sc >= 0"; return false; }
+        t.band[t.count++] = Band{nmax < 0 ? INT64_MAX : nmax, static_cast<int32_t>(r), static_cast<int32_t>(sc)};
+        p = cb + 1;
+    }
+    if (t.count == 0) { err = "no bands"; return false; }
+    t.band[t.count - 1].n_max = INT64_MAX;
+    out = t;
+    return true;
+}
+
+// Largest items-per-object ratio a table can produce for sets of up to max_n objects.
+static double items_per_object(const BandTable &t, int64_t max_n) {
+    double worst = 0.0;
+    int64_t lo = 2;
+    for (int b = 0; b < t.count && lo <= max_n; ++b) {
+        const int64_t hi = std::min(t.band[b].n_max, max_n);
+        // sample the band densely near its ends and geometrically inside
+        for (int64_t n = lo; n <= hi; n = (n < lo + 4096 ? n + 1 : n + n / 64 + 1))
+            worst = std::max(worst, static_cast<double>(items_of(t.band[b], n)) / n);
+        worst = std::max(worst, static_cast<double>(items_of(t.band[b], hi)) / hi);
+        lo = hi + 1;
+    }
+    return worst;
+}
+
+}  // namespace cc
+
+using namespace cc;
+
+struct cc_plan {
+    BandTable bands;
+    int32_t max_sets = 0;
+    int64_t max_points = 0;
+    int64_t item_cap = 0;
+    int32_t scan_blocks = 0;
+    // device buffers
+    BatchParams *d_params = nullptr;
+    BandTable *d_bands = nullptr;
+    SetDesc *d_sets = nullptr;
+    int32_t *d_cnt = nullptr;
+    uint32_t *d_flags = nullptr;
+    int64_t *d_start = nullptr;
+    int64_t *d_bsum = nullptr;
+    Item *d_items = nullptr;
+    unsigned long long *d_pcnt = nullptr;
+    double *d_psum = nullptr;
+    BatchState *d_state = nullptr;
+    // graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int main_grid = 0;
+    std::mutex mu;
+};
+
+static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
+    const int sms = sm_count();
+    k_b_prepare<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_sets, P->d_bands, P->d_cnt, P->d_flags, P->d_state);
+    k_b_scan1<<<P->scan_blocks, kScanBlock, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum);
+    k_b_scan2<<<1, kScanBlock, 0, s>>>(P->d_bsum, P->scan_blocks, P->d_state, P->item_cap);
+    k_b_emit<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_items, P->d_state);
+    k_b_main<<<P->main_grid, 256, 0, s>>>(P->d_params, P->d_sets, P->d_bands, P->d_items, P->d_state,
+                                          P->d_pcnt, P->d_psum);
+    k_b_finish<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_flags, P->d_state,
+                                       P->d_pcnt, P->d_psum);
+    CC_CUDA(cudaGetLastError());
+    return CC_OK;
+}
+
+static cc_status plan_capture(cc_plan *P) {
+    if (P->exec) return CC_OK;
+    cudaGraph_t g = nullptr;
+    CC_CUDA(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cc_status st = plan_enqueue(P, P->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(P->cap_stream, &g);
+    if (st != CC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&P->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return CC_OK;
+}
+
+// Used by the server: launches the plan's graph for sets already described in d_sets.
+cc_status plan_launch_sets(cc_plan *P, int32_t n_sets, int32_t want_sum, unsigned long long *d_counts,
+                           float *d_sums, cudaStream_t s) {
+    BatchParams bp{};
+    bp.offsets = nullptr;
+    bp.n_sets = n_sets;
+    bp.want_sum = want_sum;
+    bp.d_counts = d_counts;
+    bp.d_sums = d_sums;
+    std::lock_guard<std::mutex> lk(P->mu);
+    cc_status st = plan_capture(P);
+    if (st != CC_OK) return st;
+    CC_CUDA(cudaMemcpyAsync(P->d_params, &bp, sizeof(bp), cudaMemcpyHostToDevice, s));
+    CC_CUDA(cudaGraphLaunch(P->exec, s));
+    return CC_OK;
+}
+
+SetDesc *plan_sets_buffer(cc_plan *P) { return P->d_sets; }
+int32_t plan_max_sets(cc_plan *P) { return P->max_sets; }
+size_t plan_set_desc_bytes() { return sizeof(SetDesc); }
+
+extern "C" {
+
+cc_status cc_plan_create(cc_plan **plan, const char *tune_table_json, int32_t max_sets, int64_t max_points) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "plan is NULL");
+    *plan = nullptr;
+    if (max_sets <= 0 || max_sets > kScanBlock * kScanBlock)
+        return fail(CC_ERR_INVALID_ARG, "max_sets must be in 1..1048576");
+    if (max_points < 0) return fail(CC_ERR_INVALID_ARG, "max_points < 0");
+    cc_plan *P = new cc_plan();
+    P->bands = default_bands();
+    if (tune_table_json) {
+        std::string err;
+        if (!parse_bands(tune_table_json, P->bands, err)) {
+            delete P;
+            return fail(CC_ERR_INVALID_ARG, "tune table: " + err);
+        }
+    }
+    P->max_sets = max_sets;
+    P->max_points = max_points;
+    const double ipo = items_per_object(P->bands, std::max<int64_t>(max_points, 2));
+    P->item_cap = static_cast<int64_t>(2 * static_cast<int64_t>(max_sets) + std::ceil(ipo * max_points) + 1024);
+    P->scan_blocks = (max_sets + kScanBlock - 1) / kScanBlock;
+    auto alloc = [&](void **p, size_t b) { return cudaMalloc(p, std::max<size_t>(b, 16)); };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_params), sizeof(BatchParams));
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_bands), sizeof(BandTable));
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_sets), sizeof(SetDesc) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_cnt), sizeof(int32_t) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_flags), sizeof(uint32_t) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_start), sizeof(int64_t) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_bsum), sizeof(int64_t) * P->scan_blocks);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_items), sizeof(Item) * P->item_cap);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_pcnt), sizeof(unsigned long long) * P->item_cap);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_psum), sizeof(double) * P->item_cap);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_state), sizeof(BatchState));
+    e = e ? e : cudaMemcpy(P->d_bands, &P->bands, sizeof(BandTable), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemset(P->d_state, 0, sizeof(BatchState));
+    e = e ? e : cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cc_plan_destroy(P);
+        return fail(CC_ERR_NOMEM, std::string("plan allocation: ") + cudaGetErrorString(e));
+    }
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_b_main, 256, 0);
+    P->main_grid = sm_count() * std::max(bps, 1);
+    *plan = P;
+    return CC_OK;
+}
+
+void cc_plan_destroy(cc_plan *P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    void *bufs[] = {P->d_params, P->d_bands, P->d_sets, P->d_cnt, P->d_flags, P->d_start,
+                    P->d_bsum, P->d_items, P->d_pcnt, P->d_psum, P->d_state};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete P;
+}
+
+cc_status cc_count_pairs_batched(cc_plan *P, const cc_points *p, const int64_t *d_offsets, int32_t n_sets,
+                                 uint32_t r2, unsigned long long *d_counts, float *d_sums, void *stream) {
+    if (!P || !p || !d_offsets || !d_counts) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    if (n_sets < 0 || n_sets > P->max_sets) return fail(CC_ERR_INVALID_ARG, "n_sets outside 0..max_sets");
+    if (p->dtype != CC_I32 && p->dtype != CC_F32) return fail(CC_ERR_INVALID_ARG, "unknown dtype");
+    if (p->dtype == CC_F32 && !p->r) return fail(CC_ERR_INVALID_ARG, "radius pointer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_offsets) & 7) || (reinterpret_cast<uintptr_t>(d_counts) & 7))
+        return fail(CC_ERR_INVALID_ARG, "offsets and counts must be 8-byte aligned");
+    if (n_sets == 0) return CC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchParams bp{};
+    bp.pts = *p;
+    bp.offsets = d_offsets;
+    bp.n_sets = n_sets;
+    bp.r2 = r2;
+    bp.want_sum = d_sums != nullptr;
+    bp.d_counts = d_counts;
+    bp.d_sums = d_sums;
+    std::lock_guard<std::mutex> lk(P->mu);
+    cc_status st = plan_capture(P);
+    if (st != CC_OK) return st;
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    CC_CUDA(cudaMemcpyAsync(P->d_params, &bp, sizeof(bp), cudaMemcpyHostToDevice, s));
+    CC_CUDA(cudaGraphLaunch(P->exec, s));
+    return CC_OK;
+}
+
+cc_status cc_plan_last_items(cc_plan *P, int64_t *items) {
+    if (!P || !items) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    BatchState st{};
+    CC_CUDA(cudaDeviceSynchronize());
+    CC_CUDA(cudaMemcpy(&st, P->d_state, sizeof(st), cudaMemcpyDeviceToHost));
+    *items = st.total_items;
+    if (st.status & SET_OVERFLOW) return fail(CC_ERR_NOMEM, "work-queue capacity exceeded");
+    return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Internal declarations shared by the library's translation units (not installed).
+//
+// Device helpers: Blackwell bulk-copy (TMA engine, non-tensor form) with mbarrier
+// completion, bounded mbarrier waits, and packed FP32x2 arithmetic (sm_100+ PTX
+// add/sub/mul/fma .f32x2), all written as inline PTX.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cc.h"
+
+namespace cc {
+
+// ---------------------------------------------------------------------------------------
+// error plumbing (host)
+// ---------------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+cc_status fail(cc_status s, const std::string &msg);
+cc_status cuda_fail(cudaError_t e, const char *what);
+
+#define CC_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return ::cc::cuda_fail(e__, #call); \
+    } while (0)
+
+uint64_t wait_limit_ns();
+int debug_stall();
+int sm_count();
+
+// ---------------------------------------------------------------------------------------
+// device status bits (accumulated with atomicOr in the workspace header)
+// ---------------------------------------------------------------------------------------
+enum : uint32_t { ST_RANGE = 1u, ST_TIMEOUT = 2u };
+
+// Single-set execution modes chosen on the device by the preparation kernel.
+enum : int32_t {
+    MODE_I32_FAST = 0,   // centred int coordinates as exact FP32, expanded-square form
+    MODE_I32_WIDE = 1,   // int32 difference form (spans up to 32767)
+    MODE_RANGE_ERR = 2,  // span above 32767: nothing is counted
+    MODE_F32 = 3         // FP32 spheres
+};
+
+// Workspace header: lives at the start of each stream's scratch buffer.
+struct WsHeader {
+    uint32_t umin[3];     // order-preserving encodings of the per-axis minimum
+    uint32_t umax[3];     // ... and maximum
+    int32_t mode;         // MODE_*
+    int32_t cx, cy, cz;   // integer centre subtracted before the FP32 conversion
+    uint32_t r2e;         // r2 clamped to the largest possible squared distance
+    int32_t ai_off;       // r2e + 1 (used as n_i - ai_off), exact in FP32
+    uint32_t ticket0;     // last-block ticket of the min/max reduction
+    uint32_t ticket1;     // last-block ticket of the sum reduction
+    uint32_t status;      // ST_* bits since the last cc_stream_status()
+    uint32_t pad[17];
+};
+static_assert(sizeof(WsHeader) == 128, "header size");
+
+// Largest half-span m = ceil(span/2) for which the FP32 expanded-square form is exact:
+// every partial |n_j - 2 p_i.p_j| <= 9 m^2 and |n_i - r2e - 1| <= 12 m^2 + 1 stay
+// below 2^24.
+constexpr int32_t FAST_MAX_HALF_SPAN = 1182;
+// Integer precondition: per-axis span such that the squared distance fits in u32.
+constexpr int32_t WIDE_MAX_SPAN = 32767;
+
+// Tile configuration of the single-set kernel.
+struct SingleCfg {
+    int nt;      // consumer threads per CTA (multiple of 32)
+    int r;       // objects per consumer thread
+    int js;      // objects per staged j-stage (even)
+    int ns;      // pipeline depth (stages in shared memory)
+};
+
+// ---------------------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of *bar to complete, at most limit_ns nanoseconds (measured
+// with the global timer). Returns false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared, completion signalled on *bar (complete_tx bytes).
+// dst, src 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Packed FP32x2 arithmetic (two lanes in one 64-bit register; low word = lane 0).
+// Round to nearest even, no flush to zero, no contraction beyond the explicit fma.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_dup(float v) {
+    uint32_t u = __float_as_uint(v);
+    return (static_cast<f2>(u) << 32) | u;
+}
+__device__ __forceinline__ float f2_lo(f2 v) { return __uint_as_float(static_cast<uint32_t>(v)); }
+__device__ __forceinline__ float f2_hi(f2 v) {
+    return __uint_as_float(static_cast<uint32_t>(v >> 32));
+}
+
+// Order-preserving unsigned encoding of int32 (for atomicMin/atomicMax on u32).
+__device__ __forceinline__ uint32_t ord_enc(int32_t v) { return static_cast<uint32_t>(v) ^ 0x80000000u; }
+__device__ __forceinline__ int32_t ord_dec(uint32_t u) { return static_cast<int32_t>(u ^ 0x80000000u); }
+
+#endif  // __CUDACC__
+
+}  // namespace cc

@@ -1,0 +1,662 @@
+// Single-set kernels: the balanced cyclic pair enumeration of Section 4 (proposed
+// algorithm, with the even-N extra step), lifted to tiles for sm_103a.
+//
+// Layout in HBM (per call, in the stream's workspace):
+//   WsHeader | Rec E[nrec] | double partial[grid]
+// E is the "extended" sequence E[e] = P[e mod n] for e in [0, 2*nrec), stored as
+// pair-interleaved 32-byte records {x0,x1,y0,y1,z0,z1,w0,w1} so that (a) every j-range
+// of the cyclic schedule is one contiguous, 32-byte aligned span (no modulo in the hot
+// loop, bulk-copyable by the TMA engine) and (b) two consecutive objects j, j+1 sit in
+// 64-bit register pairs ready for the packed FP32x2 instructions.
+//
+// Work decomposition (balance is the point of the paper's scheme): the n objects are cut
+// into i-tiles of T = NT*R objects; for tile start a, object i in the tile evaluates
+// extended indices e = i+1 .. i+h_i (h_i = (n-1)/2, plus one for i < n/2 when n is
+// even). The tile's j-range [a, a+K*JS) is cut into K stages of JS objects; every
+// (tile, stage) unit holds the same T*JS candidate pairs, and each persistent CTA takes a
+// contiguous, equal share of the M*K units. Only stages that touch the first T or the
+// last T offsets of the range need the per-pair validity mask.
+//
+// Per CTA: NT consumer threads (R objects each, held in registers) plus one producer
+// warp that streams j-stages into an NS-deep shared-memory ring with cp.async.bulk and
+// mbarrier completion. Every wait is bounded (global timer) and reports CC_ERR_TIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "cc_internal.cuh"
+
+namespace cc {
+
+struct __align__(16) Rec {
+    float x[2], y[2], z[2], w[2];
+};
+static_assert(sizeof(Rec) == 32, "record size");
+
+// ---------------------------------------------------------------------------------------
+// preparation kernels
+// ---------------------------------------------------------------------------------------
+
+// Resets the per-call words of the header and the outputs.
+__global__ void k_reset(WsHeader *h, int32_t mode, unsigned long long *d_count, float *d_sum) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) {
+            h->umin[a] = 0xFFFFFFFFu;
+            h->umax[a] = 0u;
+        }
+        h->mode = mode;
+        h->cx = h->cy = h->cz = 0;
+        h->ticket0 = 0;
+        h->ticket1 = 0;
+        if (d_count) *d_count = 0ull;
+        if (d_sum) *d_sum = 0.0f;
+    }
+}
+
+// Per-axis min/max of the integer coordinates; the last block to finish derives the
+// execution mode, the integer centre and the clamped r2 (no spin: last-block ticket).
+__global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
+                         const int32_t *__restrict__ z, int64_t n, uint32_t r2, WsHeader *h,
+                         unsigned long long *d_count) {
+    uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    uint32_t mx[3] = {0u, 0u, 0u};
+    const int32_t *c[3] = {x, y, z};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            uint32_t u = ord_enc(c[a][i]);
+            mn[a] = min(mn[a], u);
+            mx[a] = max(mx[a], u);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = __reduce_min_sync(0xFFFFFFFFu, mn[a]);
+        mx[a] = __reduce_max_sync(0xFFFFFFFFu, mx[a]);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&h->umin[a], mn[a]);
+            atomicMax(&h->umax[a], mx[a]);
+        }
+    }
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&h->ticket0, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    int64_t span[3], lo[3];
+    int64_t m = 0, dmax = 0;
+    bool range_ok = true;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = ord_dec(atomicAdd(&h->umin[a], 0u));
+        int64_t hi = ord_dec(atomicAdd(&h->umax[a], 0u));
+        span[a] = hi - lo[a];
+        if (span[a] > WIDE_MAX_SPAN) range_ok = false;
+        m = max(m, (span[a] + 1) / 2);
+        dmax += span[a] * span[a];
+    }
+    int32_t mode;
+    if (!range_ok) {
+        mode = MODE_RANGE_ERR;
+        atomicOr(&h->status, ST_RANGE);
+        if (d_count) *d_count = CC_COUNT_INVALID;
+    } else if (m <= FAST_MAX_HALF_SPAN) {
+        mode = MODE_I32_FAST;
+        h->cx = static_cast<int32_t>(lo[0] + span[0] / 2);
+        h->cy = static_cast<int32_t>(lo[1] + span[1] / 2);
+        h->cz = static_cast<int32_t>(lo[2] + span[2] / 2);
+    } else {
+        mode = MODE_I32_WIDE;
+    }
+    int64_t r2e = static_cast<int64_t>(r2) < dmax ? static_cast<int64_t>(r2) : dmax;
+    h->r2e = static_cast<uint32_t>(r2e);
+    h->ai_off = static_cast<int32_t>(r2e + 1);
+    h->mode = mode;
+    h->ticket0 = 0;
+}
+
+// Fills the extended pair-interleaved array from integer SoA input.
+__global__ void k_fill_i32(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
+                           const int32_t *__restrict__ z, int64_t n, int64_t nrec,
+                           Rec *__restrict__ E, const WsHeader *__restrict__ h) {
+    const int32_t mode = h->mode;
+    if (mode == MODE_RANGE_ERR) return;
+    const int32_t cx = h->cx, cy = h->cy, cz = h->cz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrec;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        Rec rec;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            int64_t e = 2 * q + l;
+            int64_t p = e < n ? e : e % n;
+            if (mode == MODE_I32_FAST) {
+                int32_t xi = x[p] - cx, yi = y[p] - cy, zi = z[p] - cz;
+                rec.x[l] = static_cast<float>(xi);
+                rec.y[l] = static_cast<float>(yi);
+                rec.z[l] = static_cast<float>(zi);
+                rec.w[l] = static_cast<float>(xi * xi + yi * yi + zi * zi);
+            } else {
+                rec.x[l] = __int_as_float(x[p]);
+                rec.y[l] = __int_as_float(y[p]);
+                rec.z[l] = __int_as_float(z[p]);
+                rec.w[l] = 0.0f;
+            }
+        }
+        E[q] = rec;
+    }
+}
+
+// Fills the extended pair-interleaved array from FP32 sphere SoA input.
+__global__ void k_fill_f32(const float *__restrict__ x, const float *__restrict__ y,
+                           const float *__restrict__ z, const float *__restrict__ r, int64_t n,
+                           int64_t nrec, Rec *__restrict__ E) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrec;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        Rec rec;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            int64_t e = 2 * q + l;
+            int64_t p = e < n ? e : e % n;
+            rec.x[l] = x[p];
+            rec.y[l] = y[p];
+            rec.z[l] = z[p];
+            rec.w[l] = r[p];
+        }
+        E[q] = rec;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// the pair kernel
+// ---------------------------------------------------------------------------------------
+
+struct PairArgs {
+    const Rec *E;
+    int64_t n;
+    int64_t units;      // M * K
+    int32_t K;          // stages per tile
+    int32_t h;          // (n-1)/2
+    WsHeader *hdr;
+    double *partial;    // one FP64 slot per CTA (sum only)
+    unsigned long long *d_count;
+    float *d_sum;
+    uint64_t wait_ns;
+    int32_t stall;      // test hook: producer issues no copies
+    int32_t is_f32;     // 1 for FP32 spheres
+};
+
+// Register state of one consumer thread's R objects.
+template <int R>
+struct IState {
+    f2 a[R], b[R], c[R], d[R];   // packed, duplicated per-object operands
+    int32_t off[R];              // i - tile start
+    uint32_t hi[R];              // evaluations of object i (0 when i >= n)
+};
+
+__device__ __forceinline__ uint32_t sign_lo(f2 v) { return static_cast<uint32_t>(v) >> 31; }
+__device__ __forceinline__ uint32_t sign_hi(f2 v) { return static_cast<uint32_t>(v >> 63); }
+
+// Loads the R objects of consumer thread `tid` for the tile starting at `a`.
+template <int NT, int R>
+__device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t mode,
+                                       int64_t a, int tid, int32_t ai_off) {
+    const bool even = (A.n & 1) == 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int32_t off = tid + r * NT;
+        const int64_t i = a + off;
+        s.off[r] = off;
+        const bool valid = i < A.n;
+        s.hi[r] = valid ? static_cast<uint32_t>(A.h + ((even && i < A.n / 2) ? 1 : 0)) : 0u;
+        float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
+        if (valid) {
+            const Rec &q = A.E[i >> 1];
+            const int l = static_cast<int>(i & 1);
+            x = q.x[l];
+            y = q.y[l];
+            z = q.z[l];
+            w = q.w[l];
+        }
+        if (mode == MODE_I32_FAST) {
+            // t = n_j - 2 p_i.p_j through three FMAs; v = t + (n_i - r2e - 1) < 0 iff hit
+            s.a[r] = f2_dup(-2.0f * x);
+            s.b[r] = f2_dup(-2.0f * y);
+            s.c[r] = f2_dup(-2.0f * z);
+            s.d[r] = f2_dup(valid ? static_cast<float>(static_cast<int32_t>(w) - ai_off)
+                                  : __int_as_float(0x7f800000));   // +inf: never hits
+        } else if (mode == MODE_F32) {
+            s.a[r] = f2_dup(valid ? x : __int_as_float(0x7fc00000));  // NaN: never hits
+            s.b[r] = f2_dup(y);
+            s.c[r] = f2_dup(z);
+            s.d[r] = f2_dup(w);
+        } else {  // wide int: raw int32 bits
+            s.a[r] = f2_dup(x);
+            s.b[r] = f2_dup(y);
+            s.c[r] = f2_dup(z);
+            s.d[r] = 0;
+        }
+    }
+}
+
+// ---- per-pair predicates ----------------------------------------------------------------
+
+// Fast integer form, two pairs (i, j0) and (i, j1): sign bits of v mark the hits.
+__device__ __forceinline__ f2 fast_v(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulonglong2 p1) {
+    f2 t = f2_fma(a, p0.x, p1.y);
+    t = f2_fma(b, p0.y, t);
+    t = f2_fma(c, p1.x, t);
+    return f2_add(t, d);
+}
+
+// FP32 sphere predicate for two pairs, in the specified order and rounding.
+__device__ __forceinline__ void sphere_d2s2(f2 xi, f2 yi, f2 zi, f2 ri, ulonglong2 p0,
+                                            ulonglong2 p1, f2 &d2, f2 &s2) {
+    f2 dx = f2_sub(xi, p0.x);
+    f2 dy = f2_sub(yi, p0.y);
+    f2 dz = f2_sub(zi, p1.x);
+    f2 sxy = f2_add(f2_mul(dx, dx), f2_mul(dy, dy));
+    d2 = f2_add(sxy, f2_mul(dz, dz));
+    f2 s = f2_add(ri, p1.y);
+    s2 = f2_mul(s, s);
+}
+
+__device__ __forceinline__ uint32_t wide_hit(float xi, float yi, float zi, float xj, float yj,
+                                             float zj, uint32_t r2, uint32_t *d2out) {
+    int32_t dx = __float_as_int(xi) - __float_as_int(xj);
+    int32_t dy = __float_as_int(yi) - __float_as_int(yj);
+    int32_t dz = __float_as_int(zi) - __float_as_int(zj);
+    uint32_t d2 = static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy) +
+                  static_cast<uint32_t>(dz * dz);
+    *d2out = d2;
+    return d2 <= r2 ? 1u : 0u;
+}
+
+__device__ __forceinline__ double term_from_d2f(float d2) {
+    float d = __fsqrt_rn(d2);
+    return static_cast<double>(__fdiv_rn(1.0f, fmaxf(d, 1e-6f)));
+}
+
+// One stage for one consumer thread. MASKED evaluates the per-pair validity of the
+// cyclic schedule: offset s = e - i must lie in 1..h_i.
+template <int MODE, int R, int JS, bool MASKED>
+__device__ __forceinline__ uint32_t stage_count(const IState<R> &s, const ulonglong2 *st,
+                                                int32_t eo0, uint32_t r2) {
+    uint32_t cnt = 0;
+#pragma unroll 2
+    for (int q = 0; q < JS / 2; ++q) {
+        const ulonglong2 p0 = st[2 * q];
+        const ulonglong2 p1 = st[2 * q + 1];
+        const int32_t eo = eo0 + 2 * q;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            uint32_t h0, h1;
+            if (MODE == MODE_I32_FAST) {
+                f2 v = fast_v(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1);
+                h0 = sign_lo(v);
+                h1 = sign_hi(v);
+            } else if (MODE == MODE_F32) {
+                f2 d2, s2;
+                sphere_d2s2(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, d2, s2);
+                h0 = f2_lo(d2) <= f2_lo(s2) ? 1u : 0u;
+                h1 = f2_hi(d2) <= f2_hi(s2) ? 1u : 0u;
+            } else {
+                uint32_t dd;
+                h0 = wide_hit(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x),
+                              f2_lo(p0.y), f2_lo(p1.x), r2, &dd);
+                h1 = wide_hit(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_hi(p0.x),
+                              f2_hi(p0.y), f2_hi(p1.x), r2, &dd);
+            }
+            if (MASKED) {
+                const uint32_t s0 = static_cast<uint32_t>(eo - s.off[r] - 1);
+                h0 &= (s0 < s.hi[r]) ? 1u : 0u;
+                h1 &= (s0 + 1u < s.hi[r]) ? 1u : 0u;
+            }
+            cnt += h0;
+            cnt += h1;
+        }
+    }
+    return cnt;
+}
+
+// Re-walks one stage for one thread and adds the interaction terms of its hits (only
+// run when the stage's count for this thread was non-zero; hits are rare).
+template <int MODE, int R, int JS>
+__device__ double stage_terms(const IState<R> &s, const ulonglong2 *st, int32_t eo0,
+                              uint32_t r2) {
+    double sum = 0.0;
+    for (int q = 0; q < JS / 2; ++q) {
+        const ulonglong2 p0 = st[2 * q];
+        const ulonglong2 p1 = st[2 * q + 1];
+        for (int r = 0; r < R; ++r) {
+            for (int l = 0; l < 2; ++l) {
+                const uint32_t so = static_cast<uint32_t>(eo0 + 2 * q + l - s.off[r] - 1);
+                if (!(so < s.hi[r])) continue;
+                const float xj = l ? f2_hi(p0.x) : f2_lo(p0.x);
+                const float yj = l ? f2_hi(p0.y) : f2_lo(p0.y);
+                const float zj = l ? f2_hi(p1.x) : f2_lo(p1.x);
+                const float wj = l ? f2_hi(p1.y) : f2_lo(p1.y);
+                if (MODE == MODE_F32) {
+                    const float dx = __fsub_rn(f2_lo(s.a[r]), xj);
+                    const float dy = __fsub_rn(f2_lo(s.b[r]), yj);
+                    const float dz = __fsub_rn(f2_lo(s.c[r]), zj);
+                    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
+                                               __fmul_rn(dz, dz));
+                    const float sr = __fadd_rn(f2_lo(s.d[r]), wj);
+                    if (d2 <= __fmul_rn(sr, sr)) sum += term_from_d2f(d2);
+                } else if (MODE == MODE_I32_FAST) {
+                    // exact integer d2 from the centred coordinates (a = -2x etc.)
+                    const int32_t dx = static_cast<int32_t>(-0.5f * f2_lo(s.a[r])) - static_cast<int32_t>(xj);
+                    const int32_t dy = static_cast<int32_t>(-0.5f * f2_lo(s.b[r])) - static_cast<int32_t>(yj);
+                    const int32_t dz = static_cast<int32_t>(-0.5f * f2_lo(s.c[r])) - static_cast<int32_t>(zj);
+                    const uint32_t d2 = static_cast<uint32_t>(dx * dx + dy * dy + dz * dz);
+                    if (d2 <= r2) sum += term_from_d2f(static_cast<float>(d2));
+                } else {
+                    uint32_t d2;
+                    if (wide_hit(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), xj, yj, zj, r2, &d2))
+                        sum += term_from_d2f(static_cast<float>(d2));
+                }
+            }
+        }
+    }
+    return sum;
+}
+
+template <int NT, int R, int JS, int NS>
+struct SmemLayout {
+    static constexpr int kStageBytes = JS * 16;
+    static constexpr int kStages = NS * kStageBytes;
+    static constexpr int kBars = 2 * NS * 8;
+    static constexpr int kRed = (NT / 32 + 1) * 16;
+    static constexpr int kTotal = kStages + kBars + kRed + 16;
+};
+
+template <int MODE, int NT, int R, int JS, int NS, bool SUM>
+__device__ __forceinline__ void consumer_loop(const PairArgs &A, uint8_t *smem, uint64_t *full,
+                                              uint64_t *empty, volatile int *abort_flag,
+                                              int64_t u0, int64_t u1, int tid,
+                                              unsigned long long &cnt64, double &sum) {
+    constexpr int T = NT * R;
+    const int32_t ai_off = A.hdr->ai_off;
+    const uint32_t r2 = A.hdr->r2e;
+    IState<R> s;
+    int64_t cur_tile = -1;
+    const int lane = tid & 31;
+    int64_t q = 0;
+    for (int64_t u = u0; u < u1; ++u, ++q) {
+        const int64_t t = u / A.K;
+        const int32_t k = static_cast<int32_t>(u - t * A.K);
+        if (t != cur_tile) {
+            load_i<NT, R>(s, A, MODE, t * T, tid, ai_off);
+            cur_tile = t;
+        }
+        const int slot = static_cast<int>(q % NS);
+        const uint32_t par = static_cast<uint32_t>((q / NS) & 1);
+        if (!mbar_wait_bounded(&full[slot], par, A.wait_ns)) {
+            *abort_flag = 1;
+            atomicOr(&A.hdr->status, ST_TIMEOUT);
+            break;
+        }
+        if (*abort_flag) break;
+        const ulonglong2 *st =
+            reinterpret_cast<const ulonglong2 *>(smem + slot * SmemLayout<NT, R, JS, NS>::kStageBytes);
+        const int32_t eo0 = k * JS;  // offset of the stage's first object from the tile start
+        const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (eo0 + JS - 1 <= A.h);
+        uint32_t c = full_stage ? stage_count<MODE, R, JS, false>(s, st, eo0, r2)
+                                : stage_count<MODE, R, JS, true>(s, st, eo0, r2);
+        if (SUM && c != 0) sum += stage_terms<MODE, R, JS>(s, st, eo0, r2);
+        cnt64 += c;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+}
+
+template <int NT, int R, int JS, int NS, bool SUM>
+__global__ void __launch_bounds__(NT + 32) k_pairs(PairArgs A) {
+    using L = SmemLayout<NT, R, JS, NS>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kStages);
+    uint64_t *empty = full + NS;
+    unsigned long long *red_cnt = reinterpret_cast<unsigned long long *>(smem + L::kStages + L::kBars);
+    double *red_sum = reinterpret_cast<double *>(red_cnt + (NT / 32 + 1));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kStages + L::kBars + L::kRed);
+
+    const int tid = threadIdx.x;
+    const int warp = tid / 32;
+    const int32_t mode = A.is_f32 ? MODE_F32 : A.hdr->mode;
+    if (mode == MODE_RANGE_ERR) return;   // count already marked invalid
+
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], NT / 32);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int64_t G = gridDim.x;
+    const int64_t u0 = (A.units * static_cast<int64_t>(blockIdx.x)) / G;
+    const int64_t u1 = (A.units * static_cast<int64_t>(blockIdx.x + 1)) / G;
+    constexpr int T = NT * R;
+
+    unsigned long long cnt64 = 0;
+    double sum = 0.0;
+
+    if (warp == NT / 32) {
+        // producer warp: one elected lane issues the bulk copies
+        if ((tid & 31) == 0) {
+            int64_t q = 0;
+            bool ok = true;
+            for (int64_t u = u0; u < u1; ++u, ++q) {
+                const int slot = static_cast<int>(q % NS);
+                if (q >= NS) {
+                    const uint32_t par = static_cast<uint32_t>(((q / NS) - 1) & 1);
+                    if (!mbar_wait_bounded(&empty[slot], par, A.wait_ns)) {
+                        *abort_flag = 1;
+                        atomicOr(&A.hdr->status, ST_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                }
+                if (*abort_flag) { ok = false; break; }
+                if (A.stall) continue;   // test hook: nothing is copied, consumers time out
+                const int64_t t = u / A.K;
+                const int64_t k = u - t * A.K;
+                const int64_t e0 = t * T + k * JS;   // even: T and JS are even
+                mbar_arrive_expect_tx(&full[slot], L::kStageBytes);
+                bulk_g2s(smem + slot * L::kStageBytes, A.E + (e0 >> 1), L::kStageBytes, &full[slot]);
+            }
+            // before leaving, make sure no copy this CTA issued is still in flight
+            if (!A.stall) {
+                const int64_t issued = q;
+                for (int64_t qq = (issued > NS ? issued - NS : 0); qq < issued; ++qq) {
+                    const int slot = static_cast<int>(qq % NS);
+                    (void)mbar_wait_bounded(&full[slot], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
+                }
+            }
+            (void)ok;
+        }
+    } else {
+        if (mode == MODE_I32_FAST)
+            consumer_loop<MODE_I32_FAST, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
+        else if (mode == MODE_F32)
+            consumer_loop<MODE_F32, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
+        else
+            consumer_loop<MODE_I32_WIDE, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
+    }
+
+    // ---- reduction: warp shuffle -> shared memory -> one 64-bit atomic per CTA --------
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt64 += __shfl_down_sync(0xFFFFFFFFu, cnt64, o);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    }
+    if ((tid & 31) == 0) {
+        red_cnt[warp] = cnt64;
+        if (SUM) red_sum[warp] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long c = 0;
+        double sm = 0.0;
+        for (int w = 0; w < NT / 32 + 1; ++w) {
+            c += red_cnt[w];
+            if (SUM) sm += red_sum[w];
+        }
+        if (c && A.d_count) atomicAdd(A.d_count, c);
+        if (SUM) {
+            // fixed-order final reduction by the last CTA (ticket, no waiting)
+            A.partial[blockIdx.x] = sm;
+            __threadfence();
+            const unsigned ticket = atomicAdd(&A.hdr->ticket1, 1u);
+            if (ticket == gridDim.x - 1) {
+                __threadfence();
+                double tot = 0.0;
+                for (unsigned b = 0; b < gridDim.x; ++b)
+                    tot += *reinterpret_cast<volatile double *>(&A.partial[b]);
+                *A.d_sum = static_cast<float>(tot);
+                A.hdr->ticket1 = 0;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+
+struct Launch {
+    SingleCfg cfg;
+    const void *fn;
+    int smem;
+    int blocks_per_sm;
+};
+
+template <int NT, int R, int JS, int NS, bool SUM>
+static cc_status get_launch(Launch &L) {
+    static int bps = -1;
+    static int smem = SmemLayout<NT, R, JS, NS>::kTotal;
+    auto fn = k_pairs<NT, R, JS, NS, SUM>;
+    if (bps < 0) {
+        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, NT + 32, smem));
+        bps = std::max(b, 1);
+    }
+    L.cfg = SingleCfg{NT, R, JS, NS};
+    L.fn = reinterpret_cast<const void *>(fn);
+    L.smem = smem;
+    L.blocks_per_sm = bps;
+    return CC_OK;
+}
+
+// Tile shapes by size band (objects per set).
+static cc_status pick_launch(int64_t n, bool sum, Launch &L) {
+    if (n >= 65536) return sum ? get_launch<256, 8, 512, 4, true>(L) : get_launch<256, 8, 512, 4, false>(L);
+    if (n >= 2048) return sum ? get_launch<128, 4, 128, 4, true>(L) : get_launch<128, 4, 128, 4, false>(L);
+    return sum ? get_launch<64, 2, 64, 4, true>(L) : get_launch<64, 2, 64, 4, false>(L);
+}
+
+// Geometry of one call.
+struct Geometry {
+    int64_t M, K, units, nrec;
+    int grid;
+};
+
+static Geometry geometry(int64_t n, const Launch &L) {
+    Geometry g;
+    const int64_t T = static_cast<int64_t>(L.cfg.nt) * L.cfg.r;
+    const int64_t h = (n - 1) / 2;
+    g.M = (n + T - 1) / T;
+    g.K = (T + h + 1 + L.cfg.js - 1) / L.cfg.js;
+    g.units = g.M * g.K;
+    const int64_t elen = (g.M - 1) * T + g.K * L.cfg.js;
+    g.nrec = elen / 2;
+    const int64_t slots = static_cast<int64_t>(sm_count()) * L.blocks_per_sm;
+    g.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g.units, slots)));
+    return g;
+}
+
+size_t single_ws_bytes(int64_t n, bool sum) {
+    if (n < 2) return sizeof(WsHeader);
+    Launch L;
+    if (pick_launch(n, sum, L) != CC_OK) return 0;
+    Geometry g = geometry(n, L);
+    return sizeof(WsHeader) + static_cast<size_t>(g.nrec) * sizeof(Rec) +
+           static_cast<size_t>(g.grid) * sizeof(double) + 256;
+}
+
+// Enqueues the whole single-set path on `stream` using workspace `ws` (>= single_ws_bytes).
+cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
+                         float *d_sum, void *ws, cudaStream_t stream) {
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const bool f32 = p->dtype == CC_F32;
+    k_reset<<<1, 32, 0, stream>>>(hdr, f32 ? MODE_F32 : MODE_I32_FAST, d_count, d_sum);
+    CC_CUDA(cudaGetLastError());
+    if (n < 2) return CC_OK;
+    const bool sum = d_sum != nullptr;
+    Launch L;
+    cc_status st = pick_launch(n, sum, L);
+    if (st != CC_OK) return st;
+    Geometry g = geometry(n, L);
+    Rec *E = reinterpret_cast<Rec *>(reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader));
+    double *partial = reinterpret_cast<double *>(E + g.nrec);
+    const int prep_threads = 256;
+    const int64_t prep_blocks_full = (g.nrec + prep_threads - 1) / prep_threads;
+    const int prep_blocks = static_cast<int>(std::min<int64_t>(prep_blocks_full, sm_count() * 8));
+    if (!f32) {
+        const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+        k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
+                                                 static_cast<const int32_t *>(p->y),
+                                                 static_cast<const int32_t *>(p->z), n, r2, hdr,
+                                                 d_count);
+        CC_CUDA(cudaGetLastError());
+        k_fill_i32<<<prep_blocks, prep_threads, 0, stream>>>(
+            static_cast<const int32_t *>(p->x), static_cast<const int32_t *>(p->y),
+            static_cast<const int32_t *>(p->z), n, g.nrec, E, hdr);
+    } else {
+        k_fill_f32<<<prep_blocks, prep_threads, 0, stream>>>(
+            static_cast<const float *>(p->x), static_cast<const float *>(p->y),
+            static_cast<const float *>(p->z), p->r, n, g.nrec, E);
+    }
+    CC_CUDA(cudaGetLastError());
+    PairArgs A;
+    A.E = E;
+    A.n = n;
+    A.units = g.units;
+    A.K = static_cast<int32_t>(g.K);
+    A.h = static_cast<int32_t>((n - 1) / 2);
+    A.hdr = hdr;
+    A.partial = partial;
+    A.d_count = d_count;
+    A.d_sum = d_sum;
+    A.wait_ns = wait_limit_ns();
+    A.stall = debug_stall();
+    A.is_f32 = f32 ? 1 : 0;
+    void *args[] = {&A};
+    CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.cfg.nt + 32), args, L.smem, stream));
+    return CC_OK;
+}
+
+// Range check only: reset + per-axis min/max (sets ST_RANGE in the header status).
+cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t stream) {
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    k_reset<<<1, 32, 0, stream>>>(hdr, MODE_I32_FAST, nullptr, nullptr);
+    CC_CUDA(cudaGetLastError());
+    const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+    k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
+                                             static_cast<const int32_t *>(p->y),
+                                             static_cast<const int32_t *>(p->z), n, 0u, hdr, nullptr);
+    CC_CUDA(cudaGetLastError());
+    return CC_OK;
+}
+
+}  // namespace cc
