@@ -1,0 +1,530 @@
+"""Benchmark of the GB300 pair-collision path (one JSON line on stdout).
+
+Default workload (the headline): one step = the three single-set counts of the large
+integer configuration, through the C ABI:
+  N = 262144 and N = 262145 int32 points uniform in [0,1024)^3, r2 = 9, and the
+  same-cell predicate (r2 = 0) on N = 262144 points in [0,256)^3.
+metric: G pair-tests/s = sum of N(N-1)/2 over the step / device time of the step.
+
+Also measured in the same run (secondary keys of the JSON line):
+  e2e          the same step through the C ABI with host inputs: pinned host->device
+               copies and the device->host read of the counts inside the timed region;
+  roofline     dominant kernel (the pair kernel), timed with CUDA events on its stream;
+  cpu_baseline the CPU oracle (plain pairwise loop) on the host cores, full step once;
+  f32_spheres  N = 131072 FP32 spheres: count and interaction sum;
+  batched      ~100k pruned sets in one graph-captured launch vs one plain launch per set;
+  serving      Poisson queries through the continuous-batching server vs serial launches.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 run under torchrun (one process per GPU); every rank counts its own
+independently seeded sets (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "G pair-tests/s"
+WORKLOAD = ("single set N=262144 and N=262145 int32 uniform [0,1024)^3 r2=9, plus same-cell "
+            "r2=0 on N=262144 in [0,256)^3 (three counts per step)")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def pairs(n: int) -> int:
+    return n * (n - 1) // 2
+
+
+def step_inputs(rank: int = 0):
+    """The three sets of one step; rank > 0 draws independent sets (weak scaling)."""
+    sets = []
+    for n, same in ((262144, False), (262145, False), (262144, True)):
+        c = synth.cfg2(n, same_cell=same) if rank == 0 else _rank_set(n, same, rank)
+        sets.append((c["x"], c["y"], c["z"], c["r2"]))
+    return sets
+
+
+def max_over_ranks(vals, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (timing only)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def aggregate_value(tests_per_step_per_rank, world, steps, max_ms):
+    """Whole-job throughput: the pair tests all ranks processed over the slowest rank's
+    time (weak scaling: every rank has the same per-step work)."""
+    return tests_per_step_per_rank * world * steps / (max_ms * 1e-3) / 1e9
+
+
+def _rank_set(n, same, rank):
+    bits = 8 if same else 10
+    x, y, z = synth.int_points(n, bits, synth.SEED_BASE + 1000 * rank + (100 if same else 0))
+    return dict(x=x, y=y, z=z, r2=0 if same else 9)
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [v.strip() for v in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons), samples=len(sm))
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    oracle.set_threads(0)
+    cores = oracle.get_threads()
+    sets = step_inputs(0)
+    sample_n = args.ref_sample
+    work = [(x[:sample_n], y[:sample_n], z[:sample_n], r2) for (x, y, z, r2) in sets]
+    tests = sum(pairs(len(w[0])) for w in work)
+
+    def step():
+        return [oracle.count_i32(*w) for w in work]
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = tests * args.steps / dt / 1e9
+    sample = (f"first {sample_n} points of each of the three sets of the step "
+              f"({tests:.3e} pair tests per step)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline_peak_int(sms: int, mhz: float) -> float:
+    """Pair tests/s bound of the exact-integer kernel: the FP32 pipe does 128 lane-ops per
+    clock per SM and the expanded form needs 4 FP32-pipe operations per pair (three
+    products as fused multiply-adds and one add of the per-object constant)."""
+    return sms * 128.0 * mhz * 1e6 / 4.0
+
+
+def roofline_peak_f32(sms: int, mhz: float) -> float:
+    """FP32 sphere predicate: 10 FP32-pipe operations per pair (3 sub, 3 mul, 2 add,
+    radius add, radius square)."""
+    return sms * 128.0 * mhz * 1e6 / 10.0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=65536)
+    ap.add_argument("--no-extras", action="store_true", help="skip f32/batched/serving/cpu legs")
+    ap.add_argument("--serving-queries", type=int, default=20000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1901_11204_gb300 as cc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cc.build()
+    cc.lib()
+    stream = torch.cuda.current_stream()
+
+    sets = step_inputs(rank)
+    tests_per_step = sum(pairs(len(s[0])) for s in sets)
+    dsets = [tuple(torch.from_numpy(a).to(dev) for a in s[:3]) + (s[3],) for s in sets]
+    outs = [torch.empty(1, dtype=torch.int64, device=dev) for _ in sets]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    for s in dsets:
+        cc.reserve(len(s[0]))
+
+    def step():
+        for (x, y, z, r2), o in zip(dsets, outs):
+            cc.count_pairs(x, y, z, r2=r2, out=o)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    want = [cc.as_u64(o) for o in outs]
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    cc.profile_enable(True)
+    cc.profile_read()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)          # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    kern_ms, kern_launches = cc.profile_read()
+    cc.profile_enable(False)
+    clocks = sampler.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    got = [cc.as_u64(o) for o in outs]
+    assert got == want, (got, want)
+    assert cc.stream_status() == cc.CC_OK
+
+    if world > 1:
+        dev_ms, kern_ms = max_over_ranks([dev_ms, kern_ms], dist, dev)
+
+    ms_per_step = dev_ms / args.steps
+    value = aggregate_value(tests_per_step, world, args.steps, dev_ms)
+
+    # ---- roofline of the dominant kernel (pair kernel) ---------------------------------
+    peaks, peak_src = load_peaks()
+    fmax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = roofline_peak_int(sms, fmax) / 1e9
+    achieved = tests_per_step * args.steps / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+    roofline = {
+        "bound": "alu", "kernel": "k_pairs (single-set pair kernel)",
+        "achieved": achieved, "peak": peak, "unit": METRIC,
+        "frac": (achieved / peak) if achieved else None, "traffic": None,
+        "peak_basis": (f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src} sm_max_mhz) / "
+                       "4 FP32-pipe ops per pair"),
+        "kernel_share_of_step": (kern_ms / dev_ms) if dev_ms > 0 else None,
+        "kernel_launches": kern_launches,
+    }
+    if achieved and clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / fmax)
+
+    # ---- end to end through the C ABI from host buffers -------------------------------
+    hsets = [tuple(torch.from_numpy(a).pin_memory() for a in s[:3]) for s in sets]
+    hout = torch.empty(len(sets), dtype=torch.int64).pin_memory()
+    h2d = sum(sum(t.numel() * t.element_size() for t in hs) for hs in hsets)
+    d2h = hout.numel() * hout.element_size()
+
+    def e2e_step():
+        for k, ((hx, hy, hz), (x, y, z, r2)) in enumerate(zip(hsets, dsets)):
+            x.copy_(hx, non_blocking=True)
+            y.copy_(hy, non_blocking=True)
+            z.copy_(hz, non_blocking=True)
+            cc.count_pairs(x, y, z, r2=r2, out=outs[k])
+        for k in range(len(outs)):
+            hout[k:k + 1].copy_(outs[k], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k)
+        ee[k][0].record(stream)
+        e2e_step()
+        ee[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
+    assert [int(v) for v in hout.tolist()] == want
+    if world > 1:
+        e2e_ms = max_over_ranks([e2e_ms], dist, dev)[0]
+    e2e = {"value": aggregate_value(tests_per_step, world, args.steps, e2e_ms), "unit": METRIC,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": e2e_ms / args.steps}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "input_dtype": "int32 (exact: FP32 arithmetic on integers < 2^24)",
+                   "pair_tests_per_step": tests_per_step, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world} (independent sets per GPU)"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": 4 * len(sets) * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+        "counts": got,
+    }
+
+    if rank == 0 and not args.no_extras:
+        line["f32_spheres"] = bench_f32(cc, torch, dev, sms, fmax, peak_src)
+        line["batched"] = bench_batched(cc, torch, dev)
+        line["serving"] = bench_serving(cc, torch, dev, args.serving_queries)
+        line["cpu_baseline"] = cpu_baseline(sets)
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time(fn, reps, torch, stream=None):
+    stream = stream or torch.cuda.current_stream()
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_f32(cc, torch, dev, sms, fmax, peak_src):
+    c = synth.cfg3()
+    n = len(c["x"])
+    t = [torch.from_numpy(c[k]).to(dev) for k in ("x", "y", "z", "r")]
+    ms_c = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r=t[3]), 10, torch)
+    cc.profile_enable(True)
+    cc.profile_read()
+    ms_s = _time(lambda: cc.interaction_sum(t[0], t[1], t[2], r=t[3]), 10, torch)
+    kms, kl = cc.profile_read()
+    cc.profile_enable(False)
+    s, cnt = cc.interaction_sum(t[0], t[1], t[2], r=t[3])
+    torch.cuda.synchronize()
+    peak = roofline_peak_f32(sms, fmax) / 1e9
+    g_count = pairs(n) / (ms_c * 1e-3) / 1e9
+    return {"workload": f"N={n} FP32 spheres [0,1)^3 r in [0.001,0.004]",
+            "count_ms": ms_c, "count_gpairs_s": g_count,
+            "sum_ms": ms_s, "sum_gpairs_s": pairs(n) / (ms_s * 1e-3) / 1e9,
+            "count": cc.as_u64(cnt), "sum": float(s.item()),
+            "roofline_peak": peak, "count_frac": g_count / peak,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src}) / 10 FP32 ops per pair"}
+
+
+def bench_batched(cc, torch, dev):
+    c = synth.cfg4()
+    off = c["offsets"]
+    S = len(off) - 1
+    t = [torch.from_numpy(a).to(dev) for a in (c["x"], c["y"], c["z"], off)]
+    plan = cc.Plan(S, len(c["x"]))
+    holder = {}
+
+    def run():
+        holder["c"], _ = plan.count_pairs_batched(t[0], t[1], t[2], t[3], r2=c["r2"])
+
+    ms = _time(run, 20, torch)
+    items = plan.last_items()
+    n = np.diff(off)
+    tests = int((n * (n - 1) // 2).sum())
+    # plain per-set launches on the same GPU: a sample of consecutive sets, extrapolated
+    sample = 5000
+    outs = torch.empty(sample, dtype=torch.int64, device=dev)
+    xs = [(int(off[k]), int(off[k + 1])) for k in range(sample)]
+
+    def plain():
+        for k, (a, b) in enumerate(xs):
+            cc.count_pairs(t[0][a:b], t[1][a:b], t[2][a:b], r2=c["r2"], out=outs[k:k + 1])
+
+    ms_plain = _time(plain, 1, torch)
+    ok = bool((outs == holder["c"][:sample]).all().item())
+    plan.close()
+    per_set_plain_us = ms_plain / sample * 1e3
+    return {"workload": f"{S} pruned sets, {int(off[-1])} int32 points, r2={c['r2']}",
+            "ms": ms, "sets_per_s": S / (ms * 1e-3), "gpairs_s": tests / (ms * 1e-3) / 1e9,
+            "work_items": items, "pair_tests": tests,
+            "plain_us_per_set": per_set_plain_us,
+            "plain_ms_extrapolated": per_set_plain_us * S / 1e3,
+            "speedup_vs_plain": per_set_plain_us * S / 1e3 / ms,
+            "plain_sample_sets": sample, "plain_matches_batched": ok}
+
+
+def bench_serving(cc, torch, dev, nq):
+    pool = synth.cfg5_pool(2048)
+    srv = cc.Server(8 << 30, 4096)
+    ids = [srv.register_set(p["x"], p["y"], p["z"], r=p.get("r")) for p in pool]
+    # serial plain launches (one request at a time, synchronised): baseline capacity
+    dsets = [[torch.from_numpy(p[k]).to(dev) for k in (("x", "y", "z") if p["kind"] == "i32" else ("x", "y", "z", "r"))]
+             for p in pool]
+    qs = synth.cfg5_queries(nq, len(pool), 1.0)
+    ops = qs["op"]
+    sid = qs["set_id"]
+    probe = min(nq, 2000)
+
+    def serial(k):
+        s = dsets[int(sid[k])]
+        if len(s) == 3:
+            cc.count_pairs(*s, r2=9)
+        elif ops[k] == 2:
+            cc.interaction_sum(s[0], s[1], s[2], r=s[3])
+        else:
+            cc.count_pairs(s[0], s[1], s[2], r=s[3])
+        torch.cuda.synchronize()
+
+    for k in range(50):
+        serial(k)
+    lat = []
+    t0 = time.perf_counter()
+    for k in range(probe):
+        a = time.perf_counter()
+        serial(k)
+        lat.append(time.perf_counter() - a)
+    serial_rate = probe / (time.perf_counter() - t0)
+
+    def run_stream(rate):
+        q = synth.cfg5_queries(nq, len(pool), rate)
+        start = time.perf_counter()
+        t = q["t"]
+        for k in range(nq):
+            target = start + t[k]
+            while True:
+                d = target - time.perf_counter()
+                if d <= 0:
+                    break
+                if d > 2e-4:
+                    time.sleep(d - 1e-4)
+            op = cc.CC_OP_SUM if q["op"][k] == 2 else cc.CC_OP_COUNT
+            srv.submit(ids[int(q["set_id"][k])], op, 9, k)
+        srv.drain(300)
+        end = time.perf_counter()
+        res = []
+        while True:
+            g = srv.poll(65536)
+            if not g:
+                break
+            res += g
+        lat = np.array([r["t_done"] - r["t_arrive"] for r in res])
+        return {"offered_qps": rate, "queries": len(res), "achieved_qps": len(res) / (end - start),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "errors": int(sum(1 for r in res if r["status"] != 0))}
+
+    # saturation throughput: all queries offered at once
+    sat = run_stream(1e9)
+    runs = [sat]
+    for frac in (0.5, 0.8):
+        runs.append(run_stream(frac * sat["achieved_qps"]))
+    st = srv.stats()
+    srv.close()
+    return {"workload": f"{nq} Poisson queries over {len(pool)} resident sets (lognormal n in [16,65536])",
+            "serial_plain_qps": serial_rate,
+            "serial_plain_p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "serial_plain_p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "runs": runs, "server_stats": st,
+            "speedup_vs_serial": sat["achieved_qps"] / serial_rate}
+
+
+def cpu_baseline(sets):
+    import oracle
+    oracle.build()
+    oracle.set_threads(0)
+    cores = oracle.get_threads()
+    t0 = time.perf_counter()
+    for x, y, z, r2 in sets:
+        oracle.count_i32(x, y, z, r2)
+    dt = time.perf_counter() - t0
+    tests = sum(pairs(len(s[0])) for s in sets)
+    return {"value": tests / dt / 1e9, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": "the full step (all three sets) once", "seconds": dt}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

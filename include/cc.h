@@ -181,6 +181,14 @@ void cc_server_destroy(cc_server *srv);
 const char *cc_status_string(cc_status s);
 const char *cc_last_error(void);          /* thread-local message of the last failure */
 
+/* Kernel timing for benchmarks. While enabled, every launch of the single-set pair
+ * kernel is bracketed by a CUDA event pair recorded on its launching stream. */
+void cc_profile_enable(int on);
+
+/* Waits for the recorded events and returns the summed elapsed milliseconds and the
+ * number of timed launches since the previous read; then clears both. */
+cc_status cc_profile_read(double *total_ms, int64_t *launches);
+
 /* Library build identification: "cc <version> sm_103a". */
 const char *cc_version(void);
 

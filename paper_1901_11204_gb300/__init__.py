@@ -84,6 +84,8 @@ _SIGS = {
     "cc_version": ([], ctypes.c_char_p),
     "cc_set_wait_limit_ns": ([ctypes.c_uint64], None),
     "cc_debug_stall_copies": ([ctypes.c_int], None),
+    "cc_profile_enable": ([ctypes.c_int], None),
+    "cc_profile_read": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
 
 
@@ -97,8 +99,6 @@ def lib():
                                    "or python paper_1901_11204_gb300/builder.py")
             L = ctypes.CDLL(LIB_PATH)
             for name, (argt, rest) in _SIGS.items():
-                if not hasattr(L, name):
-                    continue
                 f = getattr(L, name)
                 f.argtypes = argt
                 f.restype = rest
@@ -216,6 +216,19 @@ def debug_stall_copies(on: bool):
     lib().cc_debug_stall_copies(1 if on else 0)
 
 
+def profile_enable(on: bool):
+    """Bracket every single-set pair-kernel launch with CUDA events (benchmarking)."""
+    lib().cc_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """(total kernel milliseconds, launches) since the previous read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().cc_profile_read(ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
+
+
 def version() -> str:
     return lib().cc_version().decode()
 
@@ -224,3 +237,113 @@ def as_u64(t) -> int:
     """Python int of a 1-element int64 tensor holding an unsigned 64-bit count."""
     v = int(t.item())
     return v & 0xFFFFFFFFFFFFFFFF
+
+
+# ---- batched sets ----------------------------------------------------------------------
+
+class Plan:
+    """Batching plan (cc_plan): band table + device work queue + captured graph."""
+
+    def __init__(self, max_sets: int, max_points: int, tune_table_json: str | None = None):
+        h = ctypes.c_void_p()
+        js = tune_table_json.encode() if tune_table_json else None
+        _check(lib().cc_plan_create(ctypes.byref(h), js, int(max_sets), int(max_points)))
+        self.handle = h.value
+
+    def count_pairs_batched(self, x, y, z, offsets, r2: int = 0, r=None, want_sum=False,
+                            counts=None, sums=None, stream=None):
+        """Per-set counts (int64 view of uint64) and, with want_sum, FP32 sums, for the
+        sets [offsets[k], offsets[k+1]) of the concatenated coordinates."""
+        torch = _torch()
+        pts = make_points(x, y, z, r)
+        if offsets.dtype != torch.int64 or not offsets.is_cuda:
+            raise ValueError("offsets must be an int64 CUDA tensor")
+        n_sets = offsets.numel() - 1
+        if counts is None:
+            counts = torch.empty(max(n_sets, 1), dtype=torch.int64, device=x.device)
+        if want_sum and sums is None:
+            sums = torch.empty(max(n_sets, 1), dtype=torch.float32, device=x.device)
+        _check(cc_count_pairs_batched(self.handle, pts, offsets.data_ptr(), n_sets, int(r2),
+                                      counts.data_ptr(), sums.data_ptr() if want_sum else None,
+                                      _stream_handle(stream)))
+        return counts[:n_sets], (sums[:n_sets] if want_sum else None)
+
+    def last_items(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().cc_plan_last_items(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().cc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- serving ---------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server (cc_server) over device-resident sets."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int):
+        h = ctypes.c_void_p()
+        _check(lib().cc_server_create(ctypes.byref(h), int(mem_budget_bytes), int(max_slots)))
+        self.handle = h.value
+        self._keep = []
+
+    def register_set(self, x, y, z, r=None) -> int:
+        """Copies a set (numpy arrays on the host or CUDA tensors) into device memory."""
+        import numpy as np
+
+        def ptr(a):
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            a = np.ascontiguousarray(a)
+            self._keep.append(a)
+            return a.ctypes.data
+
+        is_f32 = str(getattr(x, "dtype", "")).endswith("float32")
+        pts = cc_points(CC_F32 if is_f32 else CC_I32, ptr(x), ptr(y), ptr(z),
+                        ptr(r) if r is not None else None)
+        sid = ctypes.c_int32()
+        _check(lib().cc_server_register_set(self.handle, ctypes.byref(pts), len(x), ctypes.byref(sid)))
+        self._keep.clear()
+        return int(sid.value)
+
+    def unregister_set(self, set_id: int):
+        _check(lib().cc_server_unregister_set(self.handle, int(set_id)))
+
+    def submit(self, set_id: int, op: int, r2: int, req_id: int):
+        _check(lib().cc_server_submit(self.handle, int(set_id), int(op), int(r2), int(req_id)))
+
+    def poll(self, max_results: int = 4096):
+        buf = (cc_result * max_results)()
+        n = ctypes.c_int32()
+        _check(lib().cc_server_poll(self.handle, buf, max_results, ctypes.byref(n)))
+        return [dict(req_id=b.req_id, set_id=b.set_id, op=b.op, status=b.status, count=b.count,
+                     sum=b.sum, t_arrive=b.t_arrive_s, t_done=b.t_done_s) for b in buf[:n.value]]
+
+    def drain(self, timeout_s: float = 60.0):
+        _check(lib().cc_server_drain(self.handle, float(timeout_s)))
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib().cc_server_stats(self.handle, *[ctypes.byref(t) for t in v]))
+        return dict(batches=v[0].value, admitted=v[1].value, peak_inflight=v[2].value,
+                    peak_bytes=v[3].value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().cc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,116 @@
+"""Autotuner for the batched path: picks (R, SC) per set-size band on this GPU.
+
+For every size band it times cc_count_pairs_batched on a synthetic batch of sets whose
+sizes fall in that band, for each candidate (R objects per lane, SC steps per work item),
+and keeps the fastest. The result is a JSON table that cc_plan_create accepts:
+
+    {"gpu": "...", "sms": 152, "bands": [{"n_max": 64, "r": 1, "sc": 64}, ...],
+     "timings_ms": {...}}
+
+Tile choice never changes results (every table gives the same exact counts); it only
+changes speed. Usage:  python -m paper_1901_11204_gb300.autotune --out tune.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+
+import numpy as np
+
+DEFAULT_BANDS = [(64, 1, 64), (512, 2, 256), (8192, 4, 1024), (65536, 8, 4096), (-1, 8, 0)]
+R_CHOICES = (1, 2, 4, 8)
+SC_CHOICES = (16, 32, 64, 128, 256, 512, 1024, 2048, 4096)
+
+
+def _band_batch(lo: int, hi: int, total_points: int, seed: int):
+    rng = np.random.default_rng(seed)
+    sizes = []
+    acc = 0
+    while acc < total_points:
+        n = int(rng.integers(lo, hi + 1))
+        sizes.append(n)
+        acc += n
+    sizes = np.array(sizes, dtype=np.int64)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    n = int(off[-1])
+    x, y, z = (rng.integers(0, 48, n).astype(np.int32) for _ in range(3))
+    return x, y, z, off
+
+
+def _table(bands):
+    return json.dumps({"bands": [{"n_max": b[0], "r": b[1], "sc": b[2]} for b in bands]})
+
+
+def tune(points_per_band: int = 400_000, reps: int = 5, r_choices=R_CHOICES, sc_choices=SC_CHOICES,
+         bands=None, verbose: bool = False) -> dict:
+    import torch
+
+    from . import Plan
+
+    bands = [list(b) for b in (bands or DEFAULT_BANDS)]
+    dev = torch.device("cuda")
+    out_bands = [list(b) for b in bands]
+    timings = {}
+    lo = 2
+    for bi, (n_max, r0, sc0) in enumerate(bands):
+        hi = n_max if n_max > 0 else max(lo * 4, 131072)
+        pts = max(points_per_band, 4 * hi)
+        x, y, z, off = _band_batch(lo, hi, pts, 1000 + bi)
+        t = [torch.from_numpy(a).to(dev) for a in (x, y, z, off)]
+        best = None
+        ref = None
+        for r in r_choices:
+            for sc in (sc_choices if sc0 != 0 or bi < len(bands) - 1 else (0,) + tuple(sc_choices)):
+                cand = [list(b) for b in out_bands]
+                cand[bi] = [n_max, r, sc]
+                plan = Plan(len(off) - 1, len(x), _table(cand))
+                try:
+                    for _ in range(2):
+                        c, _ = plan.count_pairs_batched(t[0], t[1], t[2], t[3], r2=25)
+                    torch.cuda.synchronize()
+                    got = c.cpu().numpy()
+                    if ref is None:
+                        ref = got
+                    elif not np.array_equal(ref, got):
+                        raise RuntimeError(f"band {bi}: table {cand[bi]} changed the counts")
+                    ms = []
+                    for _ in range(reps):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        plan.count_pairs_batched(t[0], t[1], t[2], t[3], r2=25)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ms.append(e0.elapsed_time(e1))
+                finally:
+                    plan.close()
+                m = statistics.median(ms)
+                timings[f"band{bi}_r{r}_sc{sc}"] = m
+                if verbose:
+                    print(f"band {bi} (n <= {n_max}) r={r} sc={sc}: {m:.3f} ms", flush=True)
+                if best is None or m < best[0]:
+                    best = (m, r, sc)
+        out_bands[bi] = [n_max, best[1], best[2]]
+        lo = (n_max if n_max > 0 else hi) + 1
+    props = torch.cuda.get_device_properties(dev)
+    return {"gpu": props.name, "sms": props.multi_processor_count,
+            "bands": [{"n_max": b[0], "r": b[1], "sc": b[2]} for b in out_bands],
+            "timings_ms": timings}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="tune.json")
+    ap.add_argument("--points", type=int, default=400_000)
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+    res = tune(args.points, args.reps, verbose=True)
+    with open(args.out, "w") as f:
+        json.dump(res, f, indent=1)
+    print(json.dumps(res["bands"]))
+
+
+if __name__ == "__main__":
+    main()

@@ -9,6 +9,8 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "cc_internal.cuh"
 
@@ -36,6 +38,39 @@ cc_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 uint64_t wait_limit_ns() { return g_wait_ns.load(); }
+
+// ---- benchmark timing hook ---------------------------------------------------------------
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_pending;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+bool profiling() { return g_prof.load(); }
+
+static cudaEvent_t prof_event() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+cudaError_t profile_begin(cudaStream_t s, cudaEvent_t *e0, cudaEvent_t *e1) {
+    *e0 = prof_event();
+    *e1 = prof_event();
+    if (!*e0 || !*e1) return cudaErrorMemoryAllocation;
+    return cudaEventRecord(*e0, s);
+}
+
+void profile_end(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    cudaEventRecord(e1, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.emplace_back(e0, e1);
+}
 int debug_stall() { return g_stall.load(); }
 
 int sm_count() {
@@ -131,6 +166,36 @@ const char *cc_version(void) { return "cc 0.1 sm_103a"; }
 void cc_set_wait_limit_ns(uint64_t ns) { g_wait_ns.store(ns ? ns : 1); }
 
 void cc_debug_stall_copies(int stall) { g_stall.store(stall ? 1 : 0); }
+
+void cc_profile_enable(int on) { g_prof.store(on != 0); }
+
+cc_status cc_profile_read(double *total_ms, int64_t *launches) {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        ev.swap(g_prof_pending);
+    }
+    double tot = 0.0;
+    cudaError_t err = cudaSuccess;
+    for (auto &p : ev) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.first, p.second);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        tot += ms;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto &p : ev) {
+            g_prof_pool.push_back(p.first);
+            g_prof_pool.push_back(p.second);
+        }
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = static_cast<int64_t>(ev.size());
+    if (err != cudaSuccess) return cuda_fail(err, "cc_profile_read");
+    return CC_OK;
+}
 
 cc_status cc_reserve(int64_t max_n, void *stream) {
     if (max_n < 0) return fail(CC_ERR_INVALID_ARG, "max_n < 0");

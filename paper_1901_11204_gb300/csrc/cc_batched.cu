@@ -157,7 +157,7 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, co
         }
         if (lane == 0) {
             const int64_t it = flag == SET_OK ? items_of(band_of(*bt, d.n), d.n) : 0;
-            cnt[k] = static_cast<int32_t>(min<int64_t>(it, 0x7FFFFFFF));
+            cnt[k] = static_cast<int32_t>(it < 0x7FFFFFFF ? it : 0x7FFFFFFF);
             flags[k] = flag;
         }
     }
@@ -516,6 +516,8 @@ static cc_status plan_capture(cc_plan *P) {
     return CC_OK;
 }
 
+namespace cc {
+
 // Used by the server: launches the plan's graph for sets already described in d_sets.
 cc_status plan_launch_sets(cc_plan *P, int32_t n_sets, int32_t want_sum, unsigned long long *d_counts,
                            float *d_sums, cudaStream_t s) {
@@ -533,9 +535,10 @@ cc_status plan_launch_sets(cc_plan *P, int32_t n_sets, int32_t want_sum, unsigne
     return CC_OK;
 }
 
-SetDesc *plan_sets_buffer(cc_plan *P) { return P->d_sets; }
-int32_t plan_max_sets(cc_plan *P) { return P->max_sets; }
+void *plan_sets_buffer_v(cc_plan *P) { return P->d_sets; }
 size_t plan_set_desc_bytes() { return sizeof(SetDesc); }
+
+}  // namespace cc
 
 extern "C" {
 

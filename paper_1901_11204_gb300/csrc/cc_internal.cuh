@@ -28,6 +28,11 @@ cc_status cuda_fail(cudaError_t e, const char *what);
     } while (0)
 
 uint64_t wait_limit_ns();
+// Benchmark timing hook: true while cc_profile_enable(1); record_profiled_launch() is
+// called with the events bracketing one launch.
+bool profiling();
+cudaError_t profile_begin(cudaStream_t s, cudaEvent_t *e0, cudaEvent_t *e1);
+void profile_end(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1);
 int debug_stall();
 int sm_count();
 
@@ -104,14 +109,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// One try_wait with a suspend-time hint: the warp sleeps until the phase completes or the
+// hint (ns) elapses, instead of spinning on the barrier word.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
@@ -123,14 +130,15 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Waits for phase `parity` of *bar to complete, at most limit_ns nanoseconds (measured
-// with the global timer). Returns false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
+// with the global timer), or until *abort becomes non-zero. Returns false when the
+// bound ran out or the wait was aborted.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                                  const volatile int *abort = nullptr) {
+    if (mbar_try_wait(bar, parity, 20000u)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (;;) {
-        for (int k = 0; k < 64; ++k)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity, 200000u)) return true;
+        if (abort && *abort) return false;
         if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }

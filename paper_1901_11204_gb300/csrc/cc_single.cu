@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "cc_internal.cuh"
 
@@ -189,32 +190,39 @@ struct PairArgs {
     float *d_sum;
     uint64_t wait_ns;
     int32_t stall;      // test hook: producer issues no copies
-    int32_t is_f32;     // 1 for FP32 spheres
+    int32_t pad;
 };
 
-// Register state of one consumer thread's R objects.
+// Kernel classes: one kernel for integer points (fast exact-FP32 form or the integer
+// difference form, chosen on the device) and one for FP32 spheres.
+enum : int { CLASS_I32 = 0, CLASS_F32 = 1 };
+
+// Register state of one consumer thread's R objects: packed, duplicated operands.
+//   fast int : a = -2x, b = -2y, c = -2z, d = n_i - r2e - 1   (v = n_j - 2 p_i.p_j + d)
+//   f32      : a = x, b = y, c = z, d = r
+//   wide int : a, b, c = raw int32 bits of x, y, z
 template <int R>
 struct IState {
-    f2 a[R], b[R], c[R], d[R];   // packed, duplicated per-object operands
-    int32_t off[R];              // i - tile start
-    uint32_t hi[R];              // evaluations of object i (0 when i >= n)
+    f2 a[R], b[R], c[R], d[R];
 };
 
 __device__ __forceinline__ uint32_t sign_lo(f2 v) { return static_cast<uint32_t>(v) >> 31; }
-__device__ __forceinline__ uint32_t sign_hi(f2 v) { return static_cast<uint32_t>(v >> 63); }
+__device__ __forceinline__ uint32_t sign_hi(f2 v) { return static_cast<uint32_t>(v >> 32) >> 31; }
+
+// Evaluations of object i (0 for i >= n): (n-1)/2, plus one for i < n/2 when n is even.
+__device__ __forceinline__ uint32_t evals_of(int64_t i, int64_t n, int32_t h) {
+    if (i >= n) return 0u;
+    return static_cast<uint32_t>(h) + (((n & 1) == 0 && i < n / 2) ? 1u : 0u);
+}
 
 // Loads the R objects of consumer thread `tid` for the tile starting at `a`.
 template <int NT, int R>
-__device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t mode,
-                                       int64_t a, int tid, int32_t ai_off) {
-    const bool even = (A.n & 1) == 0;
+__device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t mode, int64_t a,
+                                       int tid, int32_t ai_off) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int32_t off = tid + r * NT;
-        const int64_t i = a + off;
-        s.off[r] = off;
+        const int64_t i = a + tid + r * NT;
         const bool valid = i < A.n;
-        s.hi[r] = valid ? static_cast<uint32_t>(A.h + ((even && i < A.n / 2) ? 1 : 0)) : 0u;
         float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
         if (valid) {
             const Rec &q = A.E[i >> 1];
@@ -225,7 +233,6 @@ __device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t 
             w = q.w[l];
         }
         if (mode == MODE_I32_FAST) {
-            // t = n_j - 2 p_i.p_j through three FMAs; v = t + (n_i - r2e - 1) < 0 iff hit
             s.a[r] = f2_dup(-2.0f * x);
             s.b[r] = f2_dup(-2.0f * y);
             s.c[r] = f2_dup(-2.0f * z);
@@ -236,7 +243,7 @@ __device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t 
             s.b[r] = f2_dup(y);
             s.c[r] = f2_dup(z);
             s.d[r] = f2_dup(w);
-        } else {  // wide int: raw int32 bits
+        } else {
             s.a[r] = f2_dup(x);
             s.b[r] = f2_dup(y);
             s.c[r] = f2_dup(z);
@@ -247,7 +254,7 @@ __device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t 
 
 // ---- per-pair predicates ----------------------------------------------------------------
 
-// Fast integer form, two pairs (i, j0) and (i, j1): sign bits of v mark the hits.
+// Fast integer form for the pairs (i, j0), (i, j1): the sign bits of v mark the hits.
 __device__ __forceinline__ f2 fast_v(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulonglong2 p1) {
     f2 t = f2_fma(a, p0.x, p1.y);
     t = f2_fma(b, p0.y, t);
@@ -267,15 +274,11 @@ __device__ __forceinline__ void sphere_d2s2(f2 xi, f2 yi, f2 zi, f2 ri, ulonglon
     s2 = f2_mul(s, s);
 }
 
-__device__ __forceinline__ uint32_t wide_hit(float xi, float yi, float zi, float xj, float yj,
-                                             float zj, uint32_t r2, uint32_t *d2out) {
+__device__ __forceinline__ uint32_t wide_d2(float xi, float yi, float zi, float xj, float yj, float zj) {
     int32_t dx = __float_as_int(xi) - __float_as_int(xj);
     int32_t dy = __float_as_int(yi) - __float_as_int(yj);
     int32_t dz = __float_as_int(zi) - __float_as_int(zj);
-    uint32_t d2 = static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy) +
-                  static_cast<uint32_t>(dz * dz);
-    *d2out = d2;
-    return d2 <= r2 ? 1u : 0u;
+    return static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy) + static_cast<uint32_t>(dz * dz);
 }
 
 __device__ __forceinline__ double term_from_d2f(float d2) {
@@ -283,22 +286,61 @@ __device__ __forceinline__ double term_from_d2f(float d2) {
     return static_cast<double>(__fdiv_rn(1.0f, fmaxf(d, 1e-6f)));
 }
 
-// One stage for one consumer thread. MASKED evaluates the per-pair validity of the
-// cyclic schedule: offset s = e - i must lie in 1..h_i.
-template <int MODE, int R, int JS, bool MASKED>
-__device__ __forceinline__ uint32_t stage_count(const IState<R> &s, const ulonglong2 *st,
-                                                int32_t eo0, uint32_t r2) {
+// Interaction terms of object slot r of this thread against the two objects of one
+// staged record (extended offsets eo, eo+1 from the tile start). Only called for record
+// groups that produced a hit (rare), so it is kept out of line.
+template <int MODE, int NT>
+__device__ __noinline__ double pair_terms(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulonglong2 p1,
+                                          int32_t eo, int32_t ioff, uint32_t evals, uint32_t r2) {
+    double sum = 0.0;
+    for (int l = 0; l < 2; ++l) {
+        const uint32_t so = static_cast<uint32_t>(eo + l - ioff - 1);
+        if (!(so < evals)) continue;
+        const float xj = l ? f2_hi(p0.x) : f2_lo(p0.x);
+        const float yj = l ? f2_hi(p0.y) : f2_lo(p0.y);
+        const float zj = l ? f2_hi(p1.x) : f2_lo(p1.x);
+        const float wj = l ? f2_hi(p1.y) : f2_lo(p1.y);
+        if (MODE == MODE_F32) {
+            const float dx = __fsub_rn(f2_lo(a), xj);
+            const float dy = __fsub_rn(f2_lo(b), yj);
+            const float dz = __fsub_rn(f2_lo(c), zj);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const float sr = __fadd_rn(f2_lo(d), wj);
+            if (d2 <= __fmul_rn(sr, sr)) sum += term_from_d2f(d2);
+        } else if (MODE == MODE_I32_FAST) {
+            // exact integer d2 from the centred coordinates (a = -2x etc.)
+            const int32_t dx = static_cast<int32_t>(-0.5f * f2_lo(a)) - static_cast<int32_t>(xj);
+            const int32_t dy = static_cast<int32_t>(-0.5f * f2_lo(b)) - static_cast<int32_t>(yj);
+            const int32_t dz = static_cast<int32_t>(-0.5f * f2_lo(c)) - static_cast<int32_t>(zj);
+            const uint32_t d2 = static_cast<uint32_t>(dx * dx + dy * dy + dz * dz);
+            if (d2 <= r2) sum += term_from_d2f(static_cast<float>(d2));
+        } else {
+            const uint32_t d2 = wide_d2(f2_lo(a), f2_lo(b), f2_lo(c), xj, yj, zj);
+            if (d2 <= r2) sum += term_from_d2f(static_cast<float>(d2));
+        }
+    }
+    return sum;
+}
+
+// One stage for one consumer thread: JS staged objects against the thread's R objects.
+// MASKED applies the cyclic schedule's validity per pair: s = e - i must be in 1..evals(i).
+// With SUM, a record group whose count moved is re-walked for its interaction terms.
+template <int MODE, int NT, int R, int JS, bool MASKED, bool SUM>
+__device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglong2 *__restrict__ st,
+                                              int32_t eo0, int tid, int64_t tile0, int64_t n,
+                                              int32_t h, uint32_t r2, double &sum) {
     uint32_t cnt = 0;
-#pragma unroll 2
+#pragma unroll(MASKED ? 1 : 2)
     for (int q = 0; q < JS / 2; ++q) {
         const ulonglong2 p0 = st[2 * q];
         const ulonglong2 p1 = st[2 * q + 1];
         const int32_t eo = eo0 + 2 * q;
+        const uint32_t before = cnt;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             uint32_t h0, h1;
             if (MODE == MODE_I32_FAST) {
-                f2 v = fast_v(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1);
+                const f2 v = fast_v(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1);
                 h0 = sign_lo(v);
                 h1 = sign_hi(v);
             } else if (MODE == MODE_F32) {
@@ -307,65 +349,31 @@ __device__ __forceinline__ uint32_t stage_count(const IState<R> &s, const ulongl
                 h0 = f2_lo(d2) <= f2_lo(s2) ? 1u : 0u;
                 h1 = f2_hi(d2) <= f2_hi(s2) ? 1u : 0u;
             } else {
-                uint32_t dd;
-                h0 = wide_hit(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x),
-                              f2_lo(p0.y), f2_lo(p1.x), r2, &dd);
-                h1 = wide_hit(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_hi(p0.x),
-                              f2_hi(p0.y), f2_hi(p1.x), r2, &dd);
+                h0 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x), f2_lo(p0.y),
+                             f2_lo(p1.x)) <= r2 ? 1u : 0u;
+                h1 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_hi(p0.x), f2_hi(p0.y),
+                             f2_hi(p1.x)) <= r2 ? 1u : 0u;
             }
             if (MASKED) {
-                const uint32_t s0 = static_cast<uint32_t>(eo - s.off[r] - 1);
-                h0 &= (s0 < s.hi[r]) ? 1u : 0u;
-                h1 &= (s0 + 1u < s.hi[r]) ? 1u : 0u;
+                const int32_t ioff = tid + r * NT;
+                const uint32_t ev = evals_of(tile0 + ioff, n, h);
+                const uint32_t s0 = static_cast<uint32_t>(eo - ioff - 1);
+                h0 &= (s0 < ev) ? 1u : 0u;
+                h1 &= (s0 + 1u < ev) ? 1u : 0u;
             }
             cnt += h0;
             cnt += h1;
         }
-    }
-    return cnt;
-}
-
-// Re-walks one stage for one thread and adds the interaction terms of its hits (only
-// run when the stage's count for this thread was non-zero; hits are rare).
-template <int MODE, int R, int JS>
-__device__ double stage_terms(const IState<R> &s, const ulonglong2 *st, int32_t eo0,
-                              uint32_t r2) {
-    double sum = 0.0;
-    for (int q = 0; q < JS / 2; ++q) {
-        const ulonglong2 p0 = st[2 * q];
-        const ulonglong2 p1 = st[2 * q + 1];
-        for (int r = 0; r < R; ++r) {
-            for (int l = 0; l < 2; ++l) {
-                const uint32_t so = static_cast<uint32_t>(eo0 + 2 * q + l - s.off[r] - 1);
-                if (!(so < s.hi[r])) continue;
-                const float xj = l ? f2_hi(p0.x) : f2_lo(p0.x);
-                const float yj = l ? f2_hi(p0.y) : f2_lo(p0.y);
-                const float zj = l ? f2_hi(p1.x) : f2_lo(p1.x);
-                const float wj = l ? f2_hi(p1.y) : f2_lo(p1.y);
-                if (MODE == MODE_F32) {
-                    const float dx = __fsub_rn(f2_lo(s.a[r]), xj);
-                    const float dy = __fsub_rn(f2_lo(s.b[r]), yj);
-                    const float dz = __fsub_rn(f2_lo(s.c[r]), zj);
-                    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
-                                               __fmul_rn(dz, dz));
-                    const float sr = __fadd_rn(f2_lo(s.d[r]), wj);
-                    if (d2 <= __fmul_rn(sr, sr)) sum += term_from_d2f(d2);
-                } else if (MODE == MODE_I32_FAST) {
-                    // exact integer d2 from the centred coordinates (a = -2x etc.)
-                    const int32_t dx = static_cast<int32_t>(-0.5f * f2_lo(s.a[r])) - static_cast<int32_t>(xj);
-                    const int32_t dy = static_cast<int32_t>(-0.5f * f2_lo(s.b[r])) - static_cast<int32_t>(yj);
-                    const int32_t dz = static_cast<int32_t>(-0.5f * f2_lo(s.c[r])) - static_cast<int32_t>(zj);
-                    const uint32_t d2 = static_cast<uint32_t>(dx * dx + dy * dy + dz * dz);
-                    if (d2 <= r2) sum += term_from_d2f(static_cast<float>(d2));
-                } else {
-                    uint32_t d2;
-                    if (wide_hit(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), xj, yj, zj, r2, &d2))
-                        sum += term_from_d2f(static_cast<float>(d2));
-                }
+        if (SUM && cnt != before) {
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                const int32_t ioff = tid + r * NT;
+                sum += pair_terms<MODE, NT>(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, eo, ioff,
+                                            evals_of(tile0 + ioff, n, h), r2);
             }
         }
     }
-    return sum;
+    return cnt;
 }
 
 template <int NT, int R, int JS, int NS>
@@ -398,27 +406,26 @@ __device__ __forceinline__ void consumer_loop(const PairArgs &A, uint8_t *smem, 
         }
         const int slot = static_cast<int>(q % NS);
         const uint32_t par = static_cast<uint32_t>((q / NS) & 1);
-        if (!mbar_wait_bounded(&full[slot], par, A.wait_ns)) {
+        if (!mbar_wait_bounded(&full[slot], par, A.wait_ns, abort_flag)) {
+            if (!*abort_flag) atomicOr(&A.hdr->status, ST_TIMEOUT);
             *abort_flag = 1;
-            atomicOr(&A.hdr->status, ST_TIMEOUT);
             break;
         }
-        if (*abort_flag) break;
         const ulonglong2 *st =
             reinterpret_cast<const ulonglong2 *>(smem + slot * SmemLayout<NT, R, JS, NS>::kStageBytes);
         const int32_t eo0 = k * JS;  // offset of the stage's first object from the tile start
         const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (eo0 + JS - 1 <= A.h);
-        uint32_t c = full_stage ? stage_count<MODE, R, JS, false>(s, st, eo0, r2)
-                                : stage_count<MODE, R, JS, true>(s, st, eo0, r2);
-        if (SUM && c != 0) sum += stage_terms<MODE, R, JS>(s, st, eo0, r2);
+        const uint32_t c =
+            full_stage ? stage_run<MODE, NT, R, JS, false, SUM>(s, st, eo0, tid, t * T, A.n, A.h, r2, sum)
+                       : stage_run<MODE, NT, R, JS, true, SUM>(s, st, eo0, tid, t * T, A.n, A.h, r2, sum);
         cnt64 += c;
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
     }
 }
 
-template <int NT, int R, int JS, int NS, bool SUM>
-__global__ void __launch_bounds__(NT + 32) k_pairs(PairArgs A) {
+template <int CLASS, int NT, int R, int JS, int NS, bool SUM, int MINB>
+__global__ void __launch_bounds__(NT + 32, MINB) k_pairs(PairArgs A) {
     using L = SmemLayout<NT, R, JS, NS>;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kStages);
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(NT + 32) k_pairs(PairArgs A) {
 
     const int tid = threadIdx.x;
     const int warp = tid / 32;
-    const int32_t mode = A.is_f32 ? MODE_F32 : A.hdr->mode;
+    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
     if (mode == MODE_RANGE_ERR) return;   // count already marked invalid
 
     if (tid == 0) {
@@ -454,19 +461,16 @@ __global__ void __launch_bounds__(NT + 32) k_pairs(PairArgs A) {
         // producer warp: one elected lane issues the bulk copies
         if ((tid & 31) == 0) {
             int64_t q = 0;
-            bool ok = true;
             for (int64_t u = u0; u < u1; ++u, ++q) {
                 const int slot = static_cast<int>(q % NS);
                 if (q >= NS) {
                     const uint32_t par = static_cast<uint32_t>(((q / NS) - 1) & 1);
-                    if (!mbar_wait_bounded(&empty[slot], par, A.wait_ns)) {
+                    if (!mbar_wait_bounded(&empty[slot], par, A.wait_ns, abort_flag)) {
+                        if (!*abort_flag) atomicOr(&A.hdr->status, ST_TIMEOUT);
                         *abort_flag = 1;
-                        atomicOr(&A.hdr->status, ST_TIMEOUT);
-                        ok = false;
                         break;
                     }
                 }
-                if (*abort_flag) { ok = false; break; }
                 if (A.stall) continue;   // test hook: nothing is copied, consumers time out
                 const int64_t t = u / A.K;
                 const int64_t k = u - t * A.K;
@@ -482,15 +486,13 @@ __global__ void __launch_bounds__(NT + 32) k_pairs(PairArgs A) {
                     (void)mbar_wait_bounded(&full[slot], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
                 }
             }
-            (void)ok;
         }
+    } else if (CLASS == CLASS_F32) {
+        consumer_loop<MODE_F32, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
+    } else if (mode == MODE_I32_FAST) {
+        consumer_loop<MODE_I32_FAST, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
     } else {
-        if (mode == MODE_I32_FAST)
-            consumer_loop<MODE_I32_FAST, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
-        else if (mode == MODE_F32)
-            consumer_loop<MODE_F32, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
-        else
-            consumer_loop<MODE_I32_WIDE, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
+        consumer_loop<MODE_I32_WIDE, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
     }
 
     // ---- reduction: warp shuffle -> shared memory -> one 64-bit atomic per CTA --------
@@ -540,11 +542,11 @@ struct Launch {
     int blocks_per_sm;
 };
 
-template <int NT, int R, int JS, int NS, bool SUM>
+template <int CLASS, int NT, int R, int JS, int NS, bool SUM, int MINB>
 static cc_status get_launch(Launch &L) {
     static int bps = -1;
     static int smem = SmemLayout<NT, R, JS, NS>::kTotal;
-    auto fn = k_pairs<NT, R, JS, NS, SUM>;
+    auto fn = k_pairs<CLASS, NT, R, JS, NS, SUM, MINB>;
     if (bps < 0) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int b = 0;
@@ -558,11 +560,30 @@ static cc_status get_launch(Launch &L) {
     return CC_OK;
 }
 
-// Tile shapes by size band (objects per set).
-static cc_status pick_launch(int64_t n, bool sum, Launch &L) {
-    if (n >= 65536) return sum ? get_launch<256, 8, 512, 4, true>(L) : get_launch<256, 8, 512, 4, false>(L);
-    if (n >= 2048) return sum ? get_launch<128, 4, 128, 4, true>(L) : get_launch<128, 4, 128, 4, false>(L);
-    return sum ? get_launch<64, 2, 64, 4, true>(L) : get_launch<64, 2, 64, 4, false>(L);
+// Tile shape of the large-set band; CC_SINGLE_VARIANT selects among the compiled shapes
+// (used by the tuning sweep; the default is the measured best).
+static int large_variant() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("CC_SINGLE_VARIANT");
+        v = e ? atoi(e) : 0;
+        if (v < 0 || v > 3) v = 0;
+    }
+    return v;
+}
+
+template <int CLASS, bool SUM>
+static cc_status pick_class(int64_t n, Launch &L) {
+    if (n >= 65536) {
+        switch (large_variant()) {
+            case 1: return get_launch<CLASS, 128, 8, 512, 6, SUM, 2>(L);
+            case 2: return get_launch<CLASS, 256, 4, 512, 6, SUM, 2>(L);
+            case 3: return get_launch<CLASS, 128, 4, 256, 8, SUM, 3>(L);
+            default: return get_launch<CLASS, 256, 8, 512, 6, SUM, 1>(L);
+        }
+    }
+    if (n >= 2048) return get_launch<CLASS, 128, 4, 128, 6, SUM, 2>(L);
+    return get_launch<CLASS, 64, 2, 64, 4, SUM, 2>(L);
 }
 
 // Geometry of one call.
@@ -585,10 +606,16 @@ static Geometry geometry(int64_t n, const Launch &L) {
     return g;
 }
 
+static cc_status pick_launch(int64_t n, bool f32, bool sum, Launch &L) {
+    if (f32) return sum ? pick_class<CLASS_F32, true>(n, L) : pick_class<CLASS_F32, false>(n, L);
+    return sum ? pick_class<CLASS_I32, true>(n, L) : pick_class<CLASS_I32, false>(n, L);
+}
+
 size_t single_ws_bytes(int64_t n, bool sum) {
     if (n < 2) return sizeof(WsHeader);
+    // the geometry depends only on the tile shape, which is the same for both classes
     Launch L;
-    if (pick_launch(n, sum, L) != CC_OK) return 0;
+    if (pick_launch(n, false, sum, L) != CC_OK) return 0;
     Geometry g = geometry(n, L);
     return sizeof(WsHeader) + static_cast<size_t>(g.nrec) * sizeof(Rec) +
            static_cast<size_t>(g.grid) * sizeof(double) + 256;
@@ -604,7 +631,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     if (n < 2) return CC_OK;
     const bool sum = d_sum != nullptr;
     Launch L;
-    cc_status st = pick_launch(n, sum, L);
+    cc_status st = pick_launch(n, f32, sum, L);
     if (st != CC_OK) return st;
     Geometry g = geometry(n, L);
     Rec *E = reinterpret_cast<Rec *>(reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader));
@@ -640,9 +667,13 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     A.d_sum = d_sum;
     A.wait_ns = wait_limit_ns();
     A.stall = debug_stall();
-    A.is_f32 = f32 ? 1 : 0;
+    A.pad = 0;
     void *args[] = {&A};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool prof = profiling();
+    if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.cfg.nt + 32), args, L.smem, stream));
+    if (prof) profile_end(stream, e0, e1);
     return CC_OK;
 }
 

@@ -1,0 +1,129 @@
+"""Serving loop: each result is the same alone and in a mix of concurrent requests, equal
+to the single-set path and the oracle; admission by memory budget and slots."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import paper_1901_11204_gb300 as cc
+    cc.build()
+    cc.lib()
+    return cc
+
+
+def pool(k=24, seed=7):
+    rng = np.random.default_rng(seed)
+    sets = []
+    for i in range(k):
+        n = int(rng.choice([2, 17, 64, 333, 1024, 4097]))
+        if i % 2 == 0:
+            x, y, z = (rng.integers(0, 20, n).astype(np.int32) for _ in range(3))
+            sets.append(("i32", x, y, z, None))
+        else:
+            x, y, z = (rng.random(n).astype(np.float32) * np.float32(0.1) for _ in range(3))
+            r = (0.002 + 0.004 * rng.random(n)).astype(np.float32)
+            sets.append(("f32", x, y, z, r))
+    return sets
+
+
+def expected(s, r2):
+    kind, x, y, z, r = s
+    if kind == "i32":
+        return oracle.count_i32(x, y, z, r2), None
+    return oracle.count_f32(x, y, z, r)
+
+
+def run_requests(srv, reqs):
+    for q in reqs:
+        srv.submit(*q)
+    srv.drain(60)
+    out = {}
+    while True:
+        got = srv.poll()
+        if not got:
+            break
+        for g in got:
+            out[g["req_id"]] = g
+    return out
+
+
+def test_alone_equals_mix_equals_oracle(cc):
+    sets = pool()
+    srv = cc.Server(1 << 30, 64)
+    ids = [srv.register_set(*s[1:4], r=s[4]) for s in sets]
+    reqs = []
+    for k, sid in enumerate(ids):
+        op = cc.CC_OP_SUM if (sets[k][0] == "f32" and k % 4 == 1) else cc.CC_OP_COUNT
+        reqs.append((sid, op, 9, k))
+    alone = {}
+    for q in reqs:
+        alone.update(run_requests(srv, [q]))
+    mix = run_requests(srv, [(a, b, c, d + 1000 * rep) for rep in range(3) for (a, b, c, d) in reqs])
+    for k, q in enumerate(reqs):
+        want_c, want_s = expected(sets[k], 9)
+        a = alone[k]
+        assert a["status"] == 0 and a["count"] == want_c, (k, a, want_c)
+        if q[1] == cc.CC_OP_SUM:
+            assert abs(a["sum"] - want_s) <= 1e-5 * max(abs(want_s), 1e-30)
+        for rep in range(3):
+            m = mix[k + 1000 * rep]
+            assert m["count"] == a["count"] and m["sum"] == a["sum"], (k, rep)
+            assert m["t_done"] >= m["t_arrive"]
+    st = srv.stats()
+    assert st["admitted"] == len(reqs) * 4
+    srv.close()
+
+
+def test_budget_and_errors(cc):
+    srv = cc.Server(200_000, 4)
+    x = np.arange(10000, dtype=np.int32)
+    sid = srv.register_set(x, x * 0, x * 0)
+    with pytest.raises(cc.CCError) as e:
+        srv.register_set(np.arange(20000, dtype=np.int32), x[:1].repeat(20000), x[:1].repeat(20000))
+    assert e.value.status == cc.CC_ERR_NOMEM
+    with pytest.raises(cc.CCError) as e:
+        srv.submit(99, cc.CC_OP_COUNT, 1, 0)
+    assert e.value.status == cc.CC_ERR_NOT_FOUND
+    # many requests through 4 slots: all complete, in-flight never exceeds the slots
+    res = run_requests(srv, [(sid, cc.CC_OP_COUNT, 1, k) for k in range(40)])
+    assert len(res) == 40 and all(r["count"] == 9999 for r in res.values())
+    assert srv.stats()["peak_inflight"] <= 4
+    srv.unregister_set(sid)
+    with pytest.raises(cc.CCError):
+        srv.submit(sid, cc.CC_OP_COUNT, 1, 0)
+    srv.close()
+
+
+def test_cfg5_pool_sample(cc):
+    p = synth.cfg5_pool(32)
+    srv = cc.Server(8 << 30, 256)
+    ids = []
+    for s in p:
+        ids.append(srv.register_set(s["x"], s["y"], s["z"], r=s.get("r")))
+    q = synth.cfg5_queries(200, len(p), 1e5)
+    reqs = []
+    for k in range(200):
+        sid = int(q["set_id"][k])
+        op = cc.CC_OP_SUM if q["op"][k] == 2 else cc.CC_OP_COUNT
+        reqs.append((ids[sid], op, 9, k))
+    res = run_requests(srv, reqs)
+    cache = {}
+    for k, (sid, op, r2, _) in enumerate(reqs):
+        s = p[int(q["set_id"][k])]
+        key = int(q["set_id"][k])
+        if key not in cache:
+            cache[key] = (oracle.count_i32(s["x"], s["y"], s["z"], 9) if s["kind"] == "i32"
+                          else oracle.count_f32(s["x"], s["y"], s["z"], s["r"]))
+        want = cache[key]
+        wc = want if isinstance(want, int) else want[0]
+        assert res[k]["count"] == wc
+        if op == cc.CC_OP_SUM:
+            assert abs(res[k]["sum"] - want[1]) <= 1e-5 * max(abs(want[1]), 1e-30)
+    srv.close()
