@@ -262,16 +262,22 @@ __device__ __forceinline__ f2 fast_v(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulon
     return f2_add(t, d);
 }
 
-// FP32 sphere predicate for two pairs, in the specified order and rounding.
+// FP32 sphere predicate for two pairs, in the specified order and rounding. The
+// differences, the radius sum and its square are packed FP32x2 operations; the squares
+// of the differences and their sums use the scalar __fmul_rn/__fadd_rn intrinsics, which
+// are never contracted into a fused multiply-add (the packed forms were observed to be
+// contracted by the code generator, which would change the rounding).
 __device__ __forceinline__ void sphere_d2s2(f2 xi, f2 yi, f2 zi, f2 ri, ulonglong2 p0,
-                                            ulonglong2 p1, f2 &d2, f2 &s2) {
-    f2 dx = f2_sub(xi, p0.x);
-    f2 dy = f2_sub(yi, p0.y);
-    f2 dz = f2_sub(zi, p1.x);
-    f2 sxy = f2_add(f2_mul(dx, dx), f2_mul(dy, dy));
-    d2 = f2_add(sxy, f2_mul(dz, dz));
-    f2 s = f2_add(ri, p1.y);
-    s2 = f2_mul(s, s);
+                                            ulonglong2 p1, float &d2lo, float &d2hi, f2 &s2) {
+    const f2 dx = f2_sub(xi, p0.x);
+    const f2 dy = f2_sub(yi, p0.y);
+    const f2 dz = f2_sub(zi, p1.x);
+    const float x0 = f2_lo(dx), x1 = f2_hi(dx), y0 = f2_lo(dy), y1 = f2_hi(dy);
+    const float z0 = f2_lo(dz), z1 = f2_hi(dz);
+    d2lo = __fadd_rn(__fadd_rn(__fmul_rn(x0, x0), __fmul_rn(y0, y0)), __fmul_rn(z0, z0));
+    d2hi = __fadd_rn(__fadd_rn(__fmul_rn(x1, x1), __fmul_rn(y1, y1)), __fmul_rn(z1, z1));
+    const f2 sr = f2_add(ri, p1.y);
+    s2 = f2_mul(sr, sr);
 }
 
 __device__ __forceinline__ uint32_t wide_d2(float xi, float yi, float zi, float xj, float yj, float zj) {
@@ -324,18 +330,29 @@ __device__ __noinline__ double pair_terms(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0,
 
 // One stage for one consumer thread: JS staged objects against the thread's R objects.
 // MASKED applies the cyclic schedule's validity per pair: s = e - i must be in 1..evals(i).
-// With SUM, a record group whose count moved is re-walked for its interaction terms.
+// With SUM, a record group that produced a hit is re-walked for its interaction terms.
+// Each object slot r has its own counter so that the accumulations do not form one long
+// dependency chain.
 template <int MODE, int NT, int R, int JS, bool MASKED, bool SUM>
 __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglong2 *__restrict__ st,
                                               int32_t eo0, int tid, int64_t tile0, int64_t n,
                                               int32_t h, uint32_t r2, double &sum) {
-    uint32_t cnt = 0;
+    uint32_t cr[R];
+    uint32_t base[R], ev[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        cr[r] = 0;
+        if (MASKED || SUM) {
+            const int32_t ioff = tid + r * NT;
+            ev[r] = evals_of(tile0 + ioff, n, h);
+            base[r] = static_cast<uint32_t>(eo0 - ioff - 1);   // s - 1 of the stage's first object
+        }
+    }
 #pragma unroll(MASKED ? 1 : 2)
     for (int q = 0; q < JS / 2; ++q) {
         const ulonglong2 p0 = st[2 * q];
         const ulonglong2 p1 = st[2 * q + 1];
-        const int32_t eo = eo0 + 2 * q;
-        const uint32_t before = cnt;
+        uint32_t any = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             uint32_t h0, h1;
@@ -344,10 +361,11 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
                 h0 = sign_lo(v);
                 h1 = sign_hi(v);
             } else if (MODE == MODE_F32) {
-                f2 d2, s2;
-                sphere_d2s2(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, d2, s2);
-                h0 = f2_lo(d2) <= f2_lo(s2) ? 1u : 0u;
-                h1 = f2_hi(d2) <= f2_hi(s2) ? 1u : 0u;
+                float d2lo, d2hi;
+                f2 s2;
+                sphere_d2s2(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, d2lo, d2hi, s2);
+                h0 = d2lo <= f2_lo(s2) ? 1u : 0u;
+                h1 = d2hi <= f2_hi(s2) ? 1u : 0u;
             } else {
                 h0 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x), f2_lo(p0.y),
                              f2_lo(p1.x)) <= r2 ? 1u : 0u;
@@ -355,24 +373,24 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
                              f2_hi(p1.x)) <= r2 ? 1u : 0u;
             }
             if (MASKED) {
-                const int32_t ioff = tid + r * NT;
-                const uint32_t ev = evals_of(tile0 + ioff, n, h);
-                const uint32_t s0 = static_cast<uint32_t>(eo - ioff - 1);
-                h0 &= (s0 < ev) ? 1u : 0u;
-                h1 &= (s0 + 1u < ev) ? 1u : 0u;
+                const uint32_t s0 = base[r] + 2u * static_cast<uint32_t>(q);
+                h0 &= (s0 < ev[r]) ? 1u : 0u;
+                h1 &= (s0 + 1u < ev[r]) ? 1u : 0u;
             }
-            cnt += h0;
-            cnt += h1;
+            cr[r] += h0;
+            cr[r] += h1;
+            if (SUM) any |= h0 | h1;
         }
-        if (SUM && cnt != before) {
+        if (SUM && any) {
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
-                const int32_t ioff = tid + r * NT;
-                sum += pair_terms<MODE, NT>(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, eo, ioff,
-                                            evals_of(tile0 + ioff, n, h), r2);
-            }
+            for (int r = 0; r < R; ++r)
+                sum += pair_terms<MODE, NT>(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, eo0 + 2 * q,
+                                            tid + r * NT, ev[r], r2);
         }
     }
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) cnt += cr[r];
     return cnt;
 }
 
@@ -532,14 +550,168 @@ __global__ void __launch_bounds__(NT + 32, MINB) k_pairs(PairArgs A) {
 }
 
 // ---------------------------------------------------------------------------------------
+// warp-independent variant: every warp owns its i-tile (32*R objects) and its own
+// NS-deep ring of j-stages, refilled by its own lane 0 with cp.async.bulk. Warps never
+// wait for each other, so a slow warp cannot stall the others, and the masked share of
+// the work shrinks with the smaller i-tile (2*32*R of every 32*R + h offsets).
+// ---------------------------------------------------------------------------------------
+
+template <int NW, int JS, int NS>
+struct WarpSmem {
+    static constexpr int kSlotBytes = JS * 16;
+    static constexpr int kPerWarp = NS * kSlotBytes;
+    static constexpr int kStages = NW * kPerWarp;
+    static constexpr int kBars = NW * NS * 8;
+    static constexpr int kRed = (NW + 1) * 16;
+    static constexpr int kTotal = kStages + kBars + kRed + 16;
+};
+
+template <int MODE, int R, int JS, int NS, bool SUM>
+__device__ __forceinline__ void warp_loop(const PairArgs &A, uint8_t *ring, uint64_t *full,
+                                          int64_t u0, int64_t u1, int lane,
+                                          unsigned long long &cnt64, double &sum) {
+    constexpr int T = 32 * R;
+    constexpr uint32_t kBytes = JS * 16;
+    const int32_t ai_off = A.hdr->ai_off;
+    const uint32_t r2 = A.hdr->r2e;
+    const bool stall = A.stall != 0;
+    int64_t issued = 0;   // copies issued (meaningful in lane 0)
+    if (lane == 0 && !stall) {
+        for (int64_t u = u0; u < u1 && u < u0 + NS; ++u) {
+            const int slot = static_cast<int>(u - u0);
+            const int64_t t = u / A.K;
+            const int64_t e0 = t * T + (u - t * A.K) * JS;
+            mbar_arrive_expect_tx(&full[slot], kBytes);
+            bulk_g2s(ring + slot * kBytes, A.E + (e0 >> 1), kBytes, &full[slot]);
+            ++issued;
+        }
+    }
+    __syncwarp();
+    IState<R> s;
+    int64_t cur_tile = -1;
+    int64_t q = 0;
+    bool timed_out = false;
+    for (int64_t u = u0; u < u1; ++u, ++q) {
+        const int64_t t = u / A.K;
+        const int32_t k = static_cast<int32_t>(u - t * A.K);
+        if (t != cur_tile) {
+            load_i<32, R>(s, A, MODE, t * T, lane, ai_off);
+            cur_tile = t;
+        }
+        const int slot = static_cast<int>(q % NS);
+        if (!mbar_wait_bounded(&full[slot], static_cast<uint32_t>((q / NS) & 1), A.wait_ns)) {
+            if (lane == 0) atomicOr(&A.hdr->status, ST_TIMEOUT);
+            timed_out = true;
+            break;
+        }
+        const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(ring + slot * kBytes);
+        const int32_t eo0 = k * JS;
+        const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (eo0 + JS - 1 <= A.h);
+        const uint32_t c =
+            full_stage ? stage_run<MODE, 32, R, JS, false, SUM>(s, st, eo0, lane, t * T, A.n, A.h, r2, sum)
+                       : stage_run<MODE, 32, R, JS, true, SUM>(s, st, eo0, lane, t * T, A.n, A.h, r2, sum);
+        cnt64 += c;
+        __syncwarp();
+        if (lane == 0 && !stall && u + NS < u1) {
+            // every lane has consumed this slot (its loads fed the arithmetic above)
+            fence_proxy_async_smem();
+            const int64_t un = u + NS;
+            const int64_t tn = un / A.K;
+            const int64_t e0 = tn * T + (un - tn * A.K) * JS;
+            mbar_arrive_expect_tx(&full[slot], kBytes);
+            bulk_g2s(ring + slot * kBytes, A.E + (e0 >> 1), kBytes, &full[slot]);
+            ++issued;
+        }
+    }
+    // after a timeout, wait (bounded) for the copies this warp issued but did not consume
+    if (timed_out && lane == 0 && !stall) {
+        for (int64_t qq = q; qq < u0 + issued - u0 && qq < q + NS; ++qq) {
+            const int sl = static_cast<int>(qq % NS);
+            (void)mbar_wait_bounded(&full[sl], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
+        }
+    }
+}
+
+template <int CLASS, int NW, int R, int JS, int NS, bool SUM, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_pairs_w(PairArgs A) {
+    using L = WarpSmem<NW, JS, NS>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    uint8_t *ring = smem + warp * L::kPerWarp;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kStages) + warp * NS;
+    unsigned long long *red_cnt = reinterpret_cast<unsigned long long *>(smem + L::kStages + L::kBars);
+    double *red_sum = reinterpret_cast<double *>(red_cnt + (NW + 1));
+
+    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
+    if (mode == MODE_RANGE_ERR) return;   // count already marked invalid
+
+    if (lane == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(&full[i], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    const int64_t W = static_cast<int64_t>(gridDim.x) * NW;
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * NW + warp;
+    const int64_t u0 = (A.units * w) / W;
+    const int64_t u1 = (A.units * (w + 1)) / W;
+
+    unsigned long long cnt64 = 0;
+    double sum = 0.0;
+    if (CLASS == CLASS_F32)
+        warp_loop<MODE_F32, R, JS, NS, SUM>(A, ring, full, u0, u1, lane, cnt64, sum);
+    else if (mode == MODE_I32_FAST)
+        warp_loop<MODE_I32_FAST, R, JS, NS, SUM>(A, ring, full, u0, u1, lane, cnt64, sum);
+    else
+        warp_loop<MODE_I32_WIDE, R, JS, NS, SUM>(A, ring, full, u0, u1, lane, cnt64, sum);
+
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt64 += __shfl_down_sync(0xFFFFFFFFu, cnt64, o);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    }
+    if (lane == 0) {
+        red_cnt[warp] = cnt64;
+        if (SUM) red_sum[warp] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long c = 0;
+        double sm = 0.0;
+        for (int i = 0; i < NW; ++i) {
+            c += red_cnt[i];
+            if (SUM) sm += red_sum[i];
+        }
+        if (c && A.d_count) atomicAdd(A.d_count, c);
+        if (SUM) {
+            A.partial[blockIdx.x] = sm;
+            __threadfence();
+            const unsigned ticket = atomicAdd(&A.hdr->ticket1, 1u);
+            if (ticket == gridDim.x - 1) {
+                __threadfence();
+                double tot = 0.0;
+                for (unsigned b = 0; b < gridDim.x; ++b)
+                    tot += *reinterpret_cast<volatile double *>(&A.partial[b]);
+                *A.d_sum = static_cast<float>(tot);
+                A.hdr->ticket1 = 0;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 
 struct Launch {
-    SingleCfg cfg;
+    SingleCfg cfg;       // nt = objects' stride inside a tile; tile = cfg.nt * cfg.r
     const void *fn;
     int smem;
     int blocks_per_sm;
+    int threads;         // threads per CTA
+    int warp_units;      // 1: units are split per warp, 0: per CTA
 };
 
 template <int CLASS, int NT, int R, int JS, int NS, bool SUM, int MINB>
@@ -557,6 +729,28 @@ static cc_status get_launch(Launch &L) {
     L.fn = reinterpret_cast<const void *>(fn);
     L.smem = smem;
     L.blocks_per_sm = bps;
+    L.threads = NT + 32;
+    L.warp_units = 0;
+    return CC_OK;
+}
+
+template <int CLASS, int NW, int R, int JS, int NS, bool SUM, int MINB>
+static cc_status get_launch_w(Launch &L) {
+    static int bps = -1;
+    static int smem = WarpSmem<NW, JS, NS>::kTotal;
+    auto fn = k_pairs_w<CLASS, NW, R, JS, NS, SUM, MINB>;
+    if (bps < 0) {
+        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, NW * 32, smem));
+        bps = std::max(b, 1);
+    }
+    L.cfg = SingleCfg{32, R, JS, NS};
+    L.fn = reinterpret_cast<const void *>(fn);
+    L.smem = smem;
+    L.blocks_per_sm = bps;
+    L.threads = NW * 32;
+    L.warp_units = 1;
     return CC_OK;
 }
 
@@ -566,8 +760,8 @@ static int large_variant() {
     static int v = -1;
     if (v < 0) {
         const char *e = getenv("CC_SINGLE_VARIANT");
-        v = e ? atoi(e) : 0;
-        if (v < 0 || v > 3) v = 0;
+        v = e ? atoi(e) : 6;
+        if (v < 0 || v > 7) v = 6;
     }
     return v;
 }
@@ -579,6 +773,10 @@ static cc_status pick_class(int64_t n, Launch &L) {
             case 1: return get_launch<CLASS, 128, 8, 512, 6, SUM, 2>(L);
             case 2: return get_launch<CLASS, 256, 4, 512, 6, SUM, 2>(L);
             case 3: return get_launch<CLASS, 128, 4, 256, 8, SUM, 3>(L);
+            case 4: return get_launch_w<CLASS, 12, 8, 256, 4, SUM, 1>(L);
+            case 5: return get_launch_w<CLASS, 16, 4, 128, 4, SUM, 1>(L);
+            case 6: return get_launch_w<CLASS, 8, 8, 256, 4, SUM, 1>(L);
+            case 7: return get_launch_w<CLASS, 16, 4, 256, 3, SUM, 1>(L);
             default: return get_launch<CLASS, 256, 8, 512, 6, SUM, 1>(L);
         }
     }
@@ -602,7 +800,8 @@ static Geometry geometry(int64_t n, const Launch &L) {
     const int64_t elen = (g.M - 1) * T + g.K * L.cfg.js;
     g.nrec = elen / 2;
     const int64_t slots = static_cast<int64_t>(sm_count()) * L.blocks_per_sm;
-    g.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g.units, slots)));
+    const int64_t per_cta = L.warp_units ? L.threads / 32 : 1;
+    g.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((g.units + per_cta - 1) / per_cta, slots)));
     return g;
 }
 
@@ -672,7 +871,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool prof = profiling();
     if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
-    CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.cfg.nt + 32), args, L.smem, stream));
+    CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.threads), args, L.smem, stream));
     if (prof) profile_end(stream, e0, e1);
     return CC_OK;
 }
