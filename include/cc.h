@@ -105,6 +105,22 @@ cc_status cc_release(void *stream);
  * it since the previous cc_stream_status(), and clears it. */
 cc_status cc_stream_status(void *stream);
 
+/* Same result as cc_count_pairs, for callers that must not allocate device memory while
+ * they run: code recording into a CUDA graph, engines whose single allocator forbids side
+ * allocations, services with a fixed memory budget that must not fail mid-run on an
+ * allocation. The paper has no counterpart; this is a deployment variant of the
+ * single-set path. Scratch is one static device array of 8 MiB inside the library,
+ * held by every GPU that loads the library until the process exits; it fits sets of
+ * about 340 thousand objects, and larger n is rejected with CC_ERR_INVALID_ARG and a
+ * message that states the exact limit. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) for that device; make that first call before
+ * any stream capture. All calls share the one array, so calls that overlap on the GPU
+ * (for example on two streams) race and give wrong counts; serialise them. Each call
+ * clears the state it needs. The count is CC_COUNT_INVALID when the device rejects the
+ * integer range. Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+cc_status cc_count_pairs_noalloc(const cc_points *p, int64_t n, uint32_t r2,
+                                 unsigned long long *d_count, void *stream);
+
 /* ---- batched sets (one persistent, graph-captured launch) --------------------------- */
 
 typedef struct cc_plan cc_plan;

@@ -61,6 +61,7 @@ _VP = ctypes.c_void_p
 _PTS = ctypes.POINTER(cc_points)
 _SIGS = {
     "cc_count_pairs": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
+    "cc_count_pairs_noalloc": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
     "cc_interaction_sum": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
     "cc_validate_points": ([_PTS, ctypes.c_int64, _VP], ctypes.c_int),
     "cc_reserve": ([ctypes.c_int64, _VP], ctypes.c_int),
