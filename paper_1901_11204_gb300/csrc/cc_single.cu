@@ -348,6 +348,45 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
             base[r] = static_cast<uint32_t>(eo0 - ioff - 1);   // s - 1 of the stage's first object
         }
     }
+    if (MODE == MODE_I32_FAST && !MASKED && !SUM) {
+        // Unmasked fast form, i-outer over blocks of QB staged record pairs: each
+        // object's coefficients are the operand repeated by consecutive instructions.
+        constexpr int QB = 4;
+#pragma unroll 1
+        for (int q0 = 0; q0 < JS / 2; q0 += QB) {
+            f2 X[QB], Y[QB], Z[QB], B[QB];
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                const ulonglong2 p0 = st[2 * (q0 + q)];
+                const ulonglong2 p1 = st[2 * (q0 + q) + 1];
+                X[q] = p0.x;
+                Y[q] = p0.y;
+                Z[q] = p1.x;
+                B[q] = p1.y;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                f2 t[QB];
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_fma(s.a[r], X[q], B[q]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_fma(s.b[r], Y[q], t[q]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_fma(s.c[r], Z[q], t[q]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_add(t[q], s.d[r]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    cr[r] += sign_lo(t[q]);
+                    cr[r] += sign_hi(t[q]);
+                }
+            }
+        }
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) cnt += cr[r];
+        return cnt;
+    }
 #pragma unroll(MASKED ? 1 : 2)
     for (int q = 0; q < JS / 2; ++q) {
         const ulonglong2 p0 = st[2 * q];
