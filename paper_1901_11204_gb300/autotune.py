@@ -1,8 +1,9 @@
 """Autotuner for the batched path: picks (R, SC) per set-size band on this GPU.
 
 For every size band it times cc_count_pairs_batched on a synthetic batch of sets whose
-sizes fall in that band, for each candidate (R objects per lane, SC steps per work item),
-and keeps the fastest. The result is a JSON table that cc_plan_create accepts:
+sizes fall in that band, for each candidate (R objects per lane, i.e. warp tiles of 32*R
+objects; SC stages of 64 objects per work item, 0 = the whole tile range), and keeps the
+fastest. The result is a JSON table that cc_plan_create accepts:
 
     {"gpu": "...", "sms": 152, "bands": [{"n_max": 64, "r": 1, "sc": 64}, ...],
      "timings_ms": {...}}
@@ -18,9 +19,9 @@ import statistics
 
 import numpy as np
 
-DEFAULT_BANDS = [(64, 1, 64), (512, 2, 256), (8192, 4, 1024), (65536, 8, 4096), (-1, 8, 0)]
-R_CHOICES = (1, 2, 4, 8)
-SC_CHOICES = (16, 32, 64, 128, 256, 512, 1024, 2048, 4096)
+DEFAULT_BANDS = [(64, 1, 0), (512, 2, 0), (8192, 4, 16), (-1, 4, 64)]
+R_CHOICES = (1, 2, 4)
+SC_CHOICES = (0, 2, 4, 8, 16, 32, 64)
 
 
 def _band_batch(lo: int, hi: int, total_points: int, seed: int):
@@ -62,7 +63,7 @@ def tune(points_per_band: int = 400_000, reps: int = 5, r_choices=R_CHOICES, sc_
         best = None
         ref = None
         for r in r_choices:
-            for sc in (sc_choices if sc0 != 0 or bi < len(bands) - 1 else (0,) + tuple(sc_choices)):
+            for sc in sc_choices:
                 cand = [list(b) for b in out_bands]
                 cand[bi] = [n_max, r, sc]
                 plan = Plan(len(off) - 1, len(x), _table(cand))

@@ -3,10 +3,14 @@
 //
 // Each set runs the proposed algorithm of Section 4 on its own: object i of a set of n
 // evaluates (i+s) mod n for s = 1..(n-1)/2, plus s = n/2 for i < n/2 when n is even.
-// Because every object does the same number of steps, a set splits into equal work
-// items along both axes: an item is (set, block of 32*R consecutive objects, chunk of
-// SC consecutive steps). R and SC come from a per-size-band table (the autotuner writes
-// it); tile choice is a pure function of (n, table), so results are reproducible.
+// A set is cut like the single-set kernel: warp tiles of 32*R objects, each with its
+// extended j-range [tile start, +K*64) cut into stages of 64 objects; a work item is
+// (set, tile, chunk of SC stages). Because every object does the same number of steps,
+// all tiles of a set carry the same work. The warp stages each 64-object j-stage into
+// its own shared-memory slot (centred exact-FP32 records for integer sets) and runs the
+// same stage loop as the single-set kernel. R and SC come from a per-size-band table
+// (the autotuner writes it); tile choice is a pure function of (n, table), so results
+// are reproducible.
 //
 // Graph (all kernels read the call's parameters from a device descriptor, so the
 // captured graph is replayed unchanged for every call):
@@ -27,16 +31,28 @@
 #include <vector>
 
 #include "cc_internal.cuh"
+#include "cc_pairs.cuh"
 
 namespace cc {
 
 constexpr int kMaxBands = 8;
 constexpr int kScanBlock = 1024;
+constexpr int kJSB = 64;          // objects per staged j-stage
+constexpr int kMainWarps = 8;     // warps per CTA of the main kernel
 
 struct Band {
     int64_t n_max;   // sets with n <= n_max (and above the previous band) use this band
-    int32_t r;       // objects per lane (1, 2, 4 or 8)
-    int32_t sc;      // steps per item; 0 = grow with n (max(4096, n/8))
+    int32_t r;       // objects per lane (1, 2 or 4): warp tile of 32*r objects
+    int32_t sc;      // stages (of 64 objects) per work item; 0 = the whole tile range
+};
+
+// Per-set execution data derived on the device by the prepare kernel.
+struct SetAux {
+    int32_t cx, cy, cz;   // integer centre (fast integer form)
+    int32_t mode;         // MODE_I32_FAST / MODE_I32_WIDE / MODE_F32
+    uint32_t r2e;         // r2 clamped to the largest possible squared distance
+    int32_t ai_off;       // r2e + 1
+    int32_t pad[2];
 };
 
 struct BandTable {
@@ -87,27 +103,29 @@ __device__ __forceinline__ const Band &band_of(const BandTable &bt, int64_t n) {
     return bt.band[bt.count - 1];
 }
 
-__host__ __device__ __forceinline__ int64_t steps_of(int64_t n) {
-    return n < 2 ? 0 : (n - 1) / 2 + ((n & 1) == 0 ? 1 : 0);
+__host__ __device__ __forceinline__ int64_t tile_of(const Band &b) { return 32 * static_cast<int64_t>(b.r); }
+
+// Stages (of kJSB objects) in one tile's extended j-range: offsets 0 .. T + h.
+__host__ __device__ __forceinline__ int64_t stages_of(const Band &b, int64_t n) {
+    const int64_t h = (n - 1) / 2;
+    return (tile_of(b) + h + 1 + kJSB - 1) / kJSB;
 }
 
-__host__ __device__ __forceinline__ int64_t sc_of(const Band &b, int64_t n) {
-    if (b.sc > 0) return b.sc;
-    int64_t v = n / 8;
-    return v > 4096 ? v : 4096;
+__host__ __device__ __forceinline__ int64_t chunks_of(const Band &b, int64_t n) {
+    const int64_t K = stages_of(b, n);
+    return b.sc > 0 ? (K + b.sc - 1) / b.sc : 1;
 }
 
 __host__ __device__ __forceinline__ int64_t items_of(const Band &b, int64_t n) {
     if (n < 2) return 0;
-    const int64_t per = 32 * static_cast<int64_t>(b.r);
-    const int64_t sc = sc_of(b, n);
-    return ((n + per - 1) / per) * ((steps_of(n) + sc - 1) / sc);
+    const int64_t T = tile_of(b);
+    return ((n + T - 1) / T) * chunks_of(b, n);
 }
 
 // ---------------------------------------------------------------------------------------
 
-__global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, const BandTable *bt,
-                            int32_t *cnt, uint32_t *flags, BatchState *st) {
+__global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, SetAux *aux,
+                            const BandTable *bt, int32_t *cnt, uint32_t *flags, BatchState *st) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -129,7 +147,7 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, co
             d.n = b - a;
             d.dtype = P->pts.dtype;
             d.r2 = P->r2;
-            if (a < 0 || b < a) {
+            if (a < 0 || b < a || b - a >= (int64_t(1) << 31)) {
                 flag = SET_BAD_OFFSETS;
                 d.n = 0;
             }
@@ -137,7 +155,9 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, co
         } else {
             d = sets[k];
         }
-        // integer range precondition, per set (span <= 32767 on every axis)
+        SetAux x{};
+        x.mode = MODE_F32;
+        // integer sets: per-axis range (precondition span <= 32767), centre, mode
         if (flag == SET_OK && d.dtype == CC_I32 && d.n >= 2) {
             uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0, 0, 0};
             const int32_t *c[3] = {static_cast<const int32_t *>(d.x), static_cast<const int32_t *>(d.y),
@@ -148,14 +168,32 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, co
                     mn[a] = min(mn[a], u);
                     mx[a] = max(mx[a], u);
                 }
+            int64_t m = 0, dmax = 0, lo[3], span[3];
             for (int a = 0; a < 3; ++a) {
                 mn[a] = __reduce_min_sync(0xFFFFFFFFu, mn[a]);
                 mx[a] = __reduce_max_sync(0xFFFFFFFFu, mx[a]);
-                if (static_cast<int64_t>(ord_dec(mx[a])) - ord_dec(mn[a]) > WIDE_MAX_SPAN)
-                    flag = SET_BAD_RANGE;
+                lo[a] = ord_dec(mn[a]);
+                span[a] = static_cast<int64_t>(ord_dec(mx[a])) - lo[a];
+                if (span[a] > WIDE_MAX_SPAN) flag = SET_BAD_RANGE;
+                m = max(m, (span[a] + 1) / 2);
+                dmax += span[a] * span[a];
             }
+            const int64_t r2e = static_cast<int64_t>(d.r2) < dmax ? static_cast<int64_t>(d.r2) : dmax;
+            x.r2e = static_cast<uint32_t>(r2e);
+            x.ai_off = static_cast<int32_t>(r2e + 1);
+            if (m <= FAST_MAX_HALF_SPAN) {
+                x.mode = MODE_I32_FAST;
+                x.cx = static_cast<int32_t>(lo[0] + span[0] / 2);
+                x.cy = static_cast<int32_t>(lo[1] + span[1] / 2);
+                x.cz = static_cast<int32_t>(lo[2] + span[2] / 2);
+            } else {
+                x.mode = MODE_I32_WIDE;
+            }
+        } else if (d.dtype == CC_I32) {
+            x.mode = MODE_I32_WIDE;
         }
         if (lane == 0) {
+            aux[k] = x;
             const int64_t it = flag == SET_OK ? items_of(band_of(*bt, d.n), d.n) : 0;
             cnt[k] = static_cast<int32_t>(it < 0x7FFFFFFF ? it : 0x7FFFFFFF);
             flags[k] = flag;
@@ -233,107 +271,134 @@ __global__ void k_b_emit(const BatchParams *__restrict__ P, const int32_t *cnt, 
 
 // ---- the per-item pair loop -------------------------------------------------------------
 
+// Loads the R objects of this lane for the tile starting at tile0 from the set's raw
+// arrays (same register conventions as the single-set kernel).
 template <int R>
-__device__ void run_item(const SetDesc &d, const Band &b, int32_t local, bool want_sum,
-                         unsigned long long &cnt_out, double &sum_out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t n = d.n;
-    const int64_t h = (n - 1) / 2;
-    const int64_t steps = steps_of(n);
-    const int64_t per = 32 * R;
-    const int64_t nbi = (n + per - 1) / per;
-    const int64_t sc = sc_of(b, n);
-    const int64_t ib = local % nbi;
-    const int64_t ch = local / nbi;
-    const int64_t s0 = ch * sc + 1;
-    const int64_t s1 = min(s0 + sc, steps + 1);
-    const int64_t half = n / 2;
-
-    int64_t iv[R];
-    bool ok[R];
-    bool first_half[R];
+__device__ __forceinline__ void load_i_raw(IState<R> &s, const SetDesc &d, const SetAux &x, int32_t tile0,
+                                           int lane) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int64_t i = ib * per + lane + 32 * r;
-        ok[r] = i < n;
-        iv[r] = ok[r] ? i : n - 1;
-        first_half[r] = iv[r] < half;
+        const int32_t i = tile0 + lane + 32 * r;
+        const bool valid = i < d.n;
+        const int32_t ii = valid ? i : 0;
+        if (x.mode == MODE_I32_FAST) {
+            const int32_t xi = static_cast<const int32_t *>(d.x)[ii] - x.cx;
+            const int32_t yi = static_cast<const int32_t *>(d.y)[ii] - x.cy;
+            const int32_t zi = static_cast<const int32_t *>(d.z)[ii] - x.cz;
+            s.a[r] = f2_dup(-2.0f * static_cast<float>(xi));
+            s.b[r] = f2_dup(-2.0f * static_cast<float>(yi));
+            s.c[r] = f2_dup(-2.0f * static_cast<float>(zi));
+            s.d[r] = f2_dup(valid ? static_cast<float>(xi * xi + yi * yi + zi * zi - x.ai_off)
+                                  : __int_as_float(0x7f800000));
+        } else if (x.mode == MODE_F32) {
+            const float xi = static_cast<const float *>(d.x)[ii];
+            s.a[r] = f2_dup(valid ? xi : __int_as_float(0x7fc00000));
+            s.b[r] = f2_dup(static_cast<const float *>(d.y)[ii]);
+            s.c[r] = f2_dup(static_cast<const float *>(d.z)[ii]);
+            s.d[r] = f2_dup(d.r[ii]);
+        } else {
+            s.a[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.x)[ii]));
+            s.b[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.y)[ii]));
+            s.c[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.z)[ii]));
+            s.d[r] = 0;
+        }
     }
-    uint32_t cnt = 0;
+}
+
+// Stages the extended objects [e0, e0 + kJSB) of the set into the warp's slot as 32
+// pair-interleaved records (lane l writes record l: objects e0+2l, e0+2l+1, mod n).
+__device__ __forceinline__ void stage_load(Rec *slot, const SetDesc &d, const SetAux &x, int32_t e0, int lane) {
+    Rec rec;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int32_t e = e0 + 2 * lane + l;
+        const int32_t p = e < d.n ? e : e % static_cast<int32_t>(d.n);
+        if (x.mode == MODE_I32_FAST) {
+            const int32_t xi = static_cast<const int32_t *>(d.x)[p] - x.cx;
+            const int32_t yi = static_cast<const int32_t *>(d.y)[p] - x.cy;
+            const int32_t zi = static_cast<const int32_t *>(d.z)[p] - x.cz;
+            rec.x[l] = static_cast<float>(xi);
+            rec.y[l] = static_cast<float>(yi);
+            rec.z[l] = static_cast<float>(zi);
+            rec.w[l] = static_cast<float>(xi * xi + yi * yi + zi * zi);
+        } else if (x.mode == MODE_F32) {
+            rec.x[l] = static_cast<const float *>(d.x)[p];
+            rec.y[l] = static_cast<const float *>(d.y)[p];
+            rec.z[l] = static_cast<const float *>(d.z)[p];
+            rec.w[l] = d.r[p];
+        } else {
+            rec.x[l] = __int_as_float(static_cast<const int32_t *>(d.x)[p]);
+            rec.y[l] = __int_as_float(static_cast<const int32_t *>(d.y)[p]);
+            rec.z[l] = __int_as_float(static_cast<const int32_t *>(d.z)[p]);
+            rec.w[l] = 0.0f;
+        }
+    }
+    slot[lane] = rec;
+}
+
+template <int MODE, int R, bool SUM>
+__device__ void run_item(const SetDesc &d, const SetAux &x, const Band &b, int32_t local, Rec *slot,
+                         unsigned long long &cnt_out, double &sum_out) {
+    const int lane = threadIdx.x & 31;
+    constexpr int T = 32 * R;
+    const int32_t n = static_cast<int32_t>(d.n);
+    const int32_t h = (n - 1) / 2;
+    const int32_t M = (n + T - 1) / T;
+    const int32_t K = static_cast<int32_t>(stages_of(b, n));
+    const int32_t tile = local % M;
+    const int32_t chunk = local / M;
+    const int32_t k0 = b.sc > 0 ? chunk * b.sc : 0;
+    const int32_t k1 = b.sc > 0 ? min(k0 + b.sc, K) : K;
+    const int32_t tile0 = tile * T;
+    IState<R> s;
+    load_i_raw<R>(s, d, x, tile0, lane);
+    const uint32_t r2 = MODE == MODE_F32 ? 0u : x.r2e;
+    const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(slot);
+    unsigned long long cnt = 0;
     double sum = 0.0;
-    if (d.dtype == CC_I32) {
-        const int32_t *X = static_cast<const int32_t *>(d.x);
-        const int32_t *Y = static_cast<const int32_t *>(d.y);
-        const int32_t *Z = static_cast<const int32_t *>(d.z);
-        int32_t xi[R], yi[R], zi[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            xi[r] = X[iv[r]];
-            yi[r] = Y[iv[r]];
-            zi[r] = Z[iv[r]];
-        }
-        for (int64_t s = s0; s < s1; ++s) {
-            const bool last_even = s > h;   // s == n/2 of an even set
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                int64_t j = iv[r] + s;
-                if (j >= n) j -= n;
-                const int32_t dx = xi[r] - __ldg(X + j);
-                const int32_t dy = yi[r] - __ldg(Y + j);
-                const int32_t dz = zi[r] - __ldg(Z + j);
-                const uint32_t d2 = static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy) +
-                                    static_cast<uint32_t>(dz * dz);
-                const bool hit = d2 <= d.r2 && ok[r] && (!last_even || first_half[r]);
-                cnt += hit ? 1u : 0u;
-                if (want_sum && hit)
-                    sum += static_cast<double>(__fdiv_rn(1.0f, fmaxf(__fsqrt_rn(static_cast<float>(d2)), 1e-6f)));
-            }
-        }
-    } else {
-        const float *X = static_cast<const float *>(d.x);
-        const float *Y = static_cast<const float *>(d.y);
-        const float *Z = static_cast<const float *>(d.z);
-        const float *Rr = d.r;
-        float xi[R], yi[R], zi[R], ri[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            xi[r] = X[iv[r]];
-            yi[r] = Y[iv[r]];
-            zi[r] = Z[iv[r]];
-            ri[r] = Rr[iv[r]];
-        }
-        for (int64_t s = s0; s < s1; ++s) {
-            const bool last_even = s > h;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                int64_t j = iv[r] + s;
-                if (j >= n) j -= n;
-                const float dx = __fsub_rn(xi[r], __ldg(X + j));
-                const float dy = __fsub_rn(yi[r], __ldg(Y + j));
-                const float dz = __fsub_rn(zi[r], __ldg(Z + j));
-                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                const float sr = __fadd_rn(ri[r], __ldg(Rr + j));
-                const bool hit = d2 <= __fmul_rn(sr, sr) && ok[r] && (!last_even || first_half[r]);
-                cnt += hit ? 1u : 0u;
-                if (want_sum && hit)
-                    sum += static_cast<double>(__fdiv_rn(1.0f, fmaxf(__fsqrt_rn(d2), 1e-6f)));
-            }
-        }
+    for (int32_t k = k0; k < k1; ++k) {
+        const int32_t eo0 = k * kJSB;
+        __syncwarp();
+        stage_load(slot, d, x, tile0 + eo0, lane);
+        __syncwarp();
+        const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (eo0 + kJSB - 1 <= h);
+        cnt += full_stage ? stage_run<MODE, 32, R, kJSB, false, SUM>(s, st, eo0, lane, tile0, n, h, r2, sum)
+                          : stage_run<MODE, 32, R, kJSB, true, SUM>(s, st, eo0, lane, tile0, n, h, r2, sum);
     }
-    // warp reduction (fixed order)
-    unsigned long long c64 = cnt;
     for (int o = 16; o > 0; o >>= 1) {
-        c64 += __shfl_down_sync(0xFFFFFFFFu, c64, o);
-        if (want_sum) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+        cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
     }
-    cnt_out = c64;
+    cnt_out = cnt;
     sum_out = sum;
 }
 
-__global__ void __launch_bounds__(256) k_b_main(const BatchParams *__restrict__ P, const SetDesc *sets,
-                                                const BandTable *bt, const Item *items, BatchState *st,
-                                                unsigned long long *pcnt, double *psum) {
+template <int R, bool SUM>
+__device__ __forceinline__ void run_item_mode(const SetDesc &d, const SetAux &x, const Band &b, int32_t local,
+                                              Rec *slot, unsigned long long &c, double &s) {
+    if (x.mode == MODE_I32_FAST) run_item<MODE_I32_FAST, R, SUM>(d, x, b, local, slot, c, s);
+    else if (x.mode == MODE_F32) run_item<MODE_F32, R, SUM>(d, x, b, local, slot, c, s);
+    else run_item<MODE_I32_WIDE, R, SUM>(d, x, b, local, slot, c, s);
+}
+
+template <bool SUM>
+__device__ __forceinline__ void run_item_r(const SetDesc &d, const SetAux &x, const Band &b, int32_t local,
+                                           Rec *slot, unsigned long long &c, double &s) {
+    switch (b.r) {
+        case 1: run_item_mode<1, SUM>(d, x, b, local, slot, c, s); break;
+        case 2: run_item_mode<2, SUM>(d, x, b, local, slot, c, s); break;
+        default: run_item_mode<4, SUM>(d, x, b, local, slot, c, s); break;
+    }
+}
+
+__global__ void __launch_bounds__(kMainWarps * 32) k_b_main(const BatchParams *__restrict__ P,
+                                                           const SetDesc *sets, const SetAux *aux,
+                                                           const BandTable *bt, const Item *items,
+                                                           BatchState *st, unsigned long long *pcnt,
+                                                           double *psum) {
+    __shared__ Rec slots[kMainWarps][kJSB / 2];
     const int lane = threadIdx.x & 31;
+    Rec *slot = slots[threadIdx.x >> 5];
     const int64_t total = st->total_items;
     const bool want_sum = P->want_sum != 0;
     for (;;) {
@@ -343,15 +408,12 @@ __global__ void __launch_bounds__(256) k_b_main(const BatchParams *__restrict__ 
         if (it >= total) break;
         const Item item = items[it];
         const SetDesc d = sets[item.set];
+        const SetAux x = aux[item.set];
         const Band b = band_of(*bt, d.n);
         unsigned long long c = 0;
         double s = 0.0;
-        switch (b.r) {
-            case 1: run_item<1>(d, b, item.local, want_sum, c, s); break;
-            case 2: run_item<2>(d, b, item.local, want_sum, c, s); break;
-            case 4: run_item<4>(d, b, item.local, want_sum, c, s); break;
-            default: run_item<8>(d, b, item.local, want_sum, c, s); break;
-        }
+        if (want_sum) run_item_r<true>(d, x, b, item.local, slot, c, s);
+        else run_item_r<false>(d, x, b, item.local, slot, c, s);
         if (lane == 0) {
             pcnt[it] = c;
             if (want_sum) psum[it] = s;
@@ -396,16 +458,16 @@ __global__ void k_b_finish(const BatchParams *__restrict__ P, const int32_t *cnt
 
 static BandTable default_bands() {
     BandTable t{};
-    t.count = 5;
-    t.band[0] = Band{64, 1, 64};
-    t.band[1] = Band{512, 2, 256};
-    t.band[2] = Band{8192, 4, 1024};
-    t.band[3] = Band{65536, 8, 4096};
-    t.band[4] = Band{INT64_MAX, 8, 0};
+    t.count = 4;
+    t.band[0] = Band{64, 1, 0};
+    t.band[1] = Band{512, 2, 0};
+    t.band[2] = Band{8192, 4, 16};
+    t.band[3] = Band{INT64_MAX, 4, 64};
     return t;
 }
 
-// Minimal parser for {"bands": [{"n_max": N, "r": R, "sc": S}, ...]} (n_max -1 = no limit).
+// Minimal parser for {"bands": [{"n_max": N, "r": R, "sc": S}, ...]} (n_max -1 = no limit;
+// r objects per lane in {1, 2, 4}; sc stages of 64 objects per work item, 0 = all).
 static bool parse_bands(const char *json, BandTable &out, std::string &err) {
     BandTable t{};
     const char *p = strstr(json, "\"bands\"");
@@ -431,7 +493,7 @@ static bool parse_bands(const char *json, BandTable &out, std::string &err) {
         long long nmax = 0, r = 0, sc = 0;
         if (!field("n_max", nmax) || !field("r", r) || !field("sc", sc)) { err = "band needs n_max, r, sc"; return false; }
         if (t.count >= kMaxBands) { err = "too many bands"; return false; }
-        if (!(r == 1 || r == 2 || r == 4 || r == 8) || sc < 0) { err = "r must be 1,2,4,8 and sc >= 0"; return false; }
+        if (!(r == 1 || r == 2 || r == 4) || sc < 0) { err = "r must be 1, 2 or 4 and sc >= 0"; return false; }
         t.band[t.count++] = Band{nmax < 0 ? INT64_MAX : nmax, static_cast<int32_t>(r), static_cast<int32_t>(sc)};
         p = cb + 1;
     }
@@ -470,6 +532,7 @@ struct cc_plan {
     BatchParams *d_params = nullptr;
     BandTable *d_bands = nullptr;
     SetDesc *d_sets = nullptr;
+    SetAux *d_aux = nullptr;
     int32_t *d_cnt = nullptr;
     uint32_t *d_flags = nullptr;
     int64_t *d_start = nullptr;
@@ -487,12 +550,13 @@ struct cc_plan {
 
 static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
     const int sms = sm_count();
-    k_b_prepare<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_sets, P->d_bands, P->d_cnt, P->d_flags, P->d_state);
+    k_b_prepare<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_sets, P->d_aux, P->d_bands, P->d_cnt, P->d_flags,
+                                        P->d_state);
     k_b_scan1<<<P->scan_blocks, kScanBlock, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum);
     k_b_scan2<<<1, kScanBlock, 0, s>>>(P->d_bsum, P->scan_blocks, P->d_state, P->item_cap);
     k_b_emit<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_items, P->d_state);
-    k_b_main<<<P->main_grid, 256, 0, s>>>(P->d_params, P->d_sets, P->d_bands, P->d_items, P->d_state,
-                                          P->d_pcnt, P->d_psum);
+    k_b_main<<<P->main_grid, kMainWarps * 32, 0, s>>>(P->d_params, P->d_sets, P->d_aux, P->d_bands, P->d_items,
+                                                       P->d_state, P->d_pcnt, P->d_psum);
     k_b_finish<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_flags, P->d_state,
                                        P->d_pcnt, P->d_psum);
     CC_CUDA(cudaGetLastError());
@@ -567,6 +631,7 @@ cc_status cc_plan_create(cc_plan **plan, const char *tune_table_json, int32_t ma
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_params), sizeof(BatchParams));
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_bands), sizeof(BandTable));
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_sets), sizeof(SetDesc) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_aux), sizeof(SetAux) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_cnt), sizeof(int32_t) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_flags), sizeof(uint32_t) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_start), sizeof(int64_t) * max_sets);
@@ -583,7 +648,7 @@ cc_status cc_plan_create(cc_plan **plan, const char *tune_table_json, int32_t ma
         return fail(CC_ERR_NOMEM, std::string("plan allocation: ") + cudaGetErrorString(e));
     }
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_b_main, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_b_main, kMainWarps * 32, 0);
     P->main_grid = sm_count() * std::max(bps, 1);
     *plan = P;
     return CC_OK;
@@ -593,7 +658,7 @@ void cc_plan_destroy(cc_plan *P) {
     if (!P) return;
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
-    void *bufs[] = {P->d_params, P->d_bands, P->d_sets, P->d_cnt, P->d_flags, P->d_start,
+    void *bufs[] = {P->d_params, P->d_bands, P->d_sets, P->d_aux, P->d_cnt, P->d_flags, P->d_start,
                     P->d_bsum, P->d_items, P->d_pcnt, P->d_psum, P->d_state};
     for (void *b : bufs)
         if (b) cudaFree(b);

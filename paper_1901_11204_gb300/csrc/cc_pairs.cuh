@@ -1,0 +1,211 @@
+// Device-side pieces of the pair test shared by the single-set and the batched kernels:
+// the staged record layout, the per-object register state and one stage of the cyclic
+// schedule (Section 4, proposed algorithm) for one warp's objects.
+#pragma once
+
+#include "cc_internal.cuh"
+
+namespace cc {
+
+struct __align__(16) Rec {
+    float x[2], y[2], z[2], w[2];
+};
+static_assert(sizeof(Rec) == 32, "record size");
+
+// Register state of one consumer thread's R objects: packed, duplicated operands.
+//   fast int : a = -2x, b = -2y, c = -2z, d = n_i - r2e - 1   (v = n_j - 2 p_i.p_j + d)
+//   f32      : a = x, b = y, c = z, d = r
+//   wide int : a, b, c = raw int32 bits of x, y, z
+template <int R>
+struct IState {
+    f2 a[R], b[R], c[R], d[R];
+};
+
+__device__ __forceinline__ uint32_t sign_lo(f2 v) { return static_cast<uint32_t>(v) >> 31; }
+__device__ __forceinline__ uint32_t sign_hi(f2 v) { return static_cast<uint32_t>(v >> 32) >> 31; }
+
+// Evaluations of object i (0 for i >= n): (n-1)/2, plus one for i < n/2 when n is even.
+__device__ __forceinline__ uint32_t evals_of(int64_t i, int64_t n, int32_t h) {
+    if (i >= n) return 0u;
+    return static_cast<uint32_t>(h) + (((n & 1) == 0 && i < n / 2) ? 1u : 0u);
+}
+
+// ---- per-pair predicates ----------------------------------------------------------------
+
+// Fast integer form for the pairs (i, j0), (i, j1): the sign bits of v mark the hits.
+__device__ __forceinline__ f2 fast_v(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulonglong2 p1) {
+    f2 t = f2_fma(a, p0.x, p1.y);
+    t = f2_fma(b, p0.y, t);
+    t = f2_fma(c, p1.x, t);
+    return f2_add(t, d);
+}
+
+// FP32 sphere predicate for two pairs, in the specified order and rounding. The
+// differences, the radius sum and its square are packed FP32x2 operations; the squares
+// of the differences and their sums use the scalar __fmul_rn/__fadd_rn intrinsics, which
+// are never contracted into a fused multiply-add (the packed forms were observed to be
+// contracted by the code generator, which would change the rounding).
+__device__ __forceinline__ void sphere_d2s2(f2 xi, f2 yi, f2 zi, f2 ri, ulonglong2 p0,
+                                            ulonglong2 p1, float &d2lo, float &d2hi, f2 &s2) {
+    const f2 dx = f2_sub(xi, p0.x);
+    const f2 dy = f2_sub(yi, p0.y);
+    const f2 dz = f2_sub(zi, p1.x);
+    const float x0 = f2_lo(dx), x1 = f2_hi(dx), y0 = f2_lo(dy), y1 = f2_hi(dy);
+    const float z0 = f2_lo(dz), z1 = f2_hi(dz);
+    d2lo = __fadd_rn(__fadd_rn(__fmul_rn(x0, x0), __fmul_rn(y0, y0)), __fmul_rn(z0, z0));
+    d2hi = __fadd_rn(__fadd_rn(__fmul_rn(x1, x1), __fmul_rn(y1, y1)), __fmul_rn(z1, z1));
+    const f2 sr = f2_add(ri, p1.y);
+    s2 = f2_mul(sr, sr);
+}
+
+__device__ __forceinline__ uint32_t wide_d2(float xi, float yi, float zi, float xj, float yj, float zj) {
+    int32_t dx = __float_as_int(xi) - __float_as_int(xj);
+    int32_t dy = __float_as_int(yi) - __float_as_int(yj);
+    int32_t dz = __float_as_int(zi) - __float_as_int(zj);
+    return static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy) + static_cast<uint32_t>(dz * dz);
+}
+
+__device__ __forceinline__ double term_from_d2f(float d2) {
+    float d = __fsqrt_rn(d2);
+    return static_cast<double>(__fdiv_rn(1.0f, fmaxf(d, 1e-6f)));
+}
+
+// Interaction terms of object slot r of this thread against the two objects of one
+// staged record (extended offsets eo, eo+1 from the tile start). Only called for record
+// groups that produced a hit (rare), so it is kept out of line.
+template <int MODE, int NT>
+__device__ __noinline__ double pair_terms(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulonglong2 p1,
+                                          int32_t eo, int32_t ioff, uint32_t evals, uint32_t r2) {
+    double sum = 0.0;
+    for (int l = 0; l < 2; ++l) {
+        const uint32_t so = static_cast<uint32_t>(eo + l - ioff - 1);
+        if (!(so < evals)) continue;
+        const float xj = l ? f2_hi(p0.x) : f2_lo(p0.x);
+        const float yj = l ? f2_hi(p0.y) : f2_lo(p0.y);
+        const float zj = l ? f2_hi(p1.x) : f2_lo(p1.x);
+        const float wj = l ? f2_hi(p1.y) : f2_lo(p1.y);
+        if (MODE == MODE_F32) {
+            const float dx = __fsub_rn(f2_lo(a), xj);
+            const float dy = __fsub_rn(f2_lo(b), yj);
+            const float dz = __fsub_rn(f2_lo(c), zj);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const float sr = __fadd_rn(f2_lo(d), wj);
+            if (d2 <= __fmul_rn(sr, sr)) sum += term_from_d2f(d2);
+        } else if (MODE == MODE_I32_FAST) {
+            // exact integer d2 from the centred coordinates (a = -2x etc.)
+            const int32_t dx = static_cast<int32_t>(-0.5f * f2_lo(a)) - static_cast<int32_t>(xj);
+            const int32_t dy = static_cast<int32_t>(-0.5f * f2_lo(b)) - static_cast<int32_t>(yj);
+            const int32_t dz = static_cast<int32_t>(-0.5f * f2_lo(c)) - static_cast<int32_t>(zj);
+            const uint32_t d2 = static_cast<uint32_t>(dx * dx + dy * dy + dz * dz);
+            if (d2 <= r2) sum += term_from_d2f(static_cast<float>(d2));
+        } else {
+            const uint32_t d2 = wide_d2(f2_lo(a), f2_lo(b), f2_lo(c), xj, yj, zj);
+            if (d2 <= r2) sum += term_from_d2f(static_cast<float>(d2));
+        }
+    }
+    return sum;
+}
+
+// One stage for one consumer thread: JS staged objects against the thread's R objects.
+// MASKED applies the cyclic schedule's validity per pair: s = e - i must be in 1..evals(i).
+// With SUM, a record group that produced a hit is re-walked for its interaction terms.
+// Each object slot r has its own counter so that the accumulations do not form one long
+// dependency chain.
+template <int MODE, int NT, int R, int JS, bool MASKED, bool SUM>
+__device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglong2 *__restrict__ st,
+                                              int32_t eo0, int tid, int64_t tile0, int64_t n,
+                                              int32_t h, uint32_t r2, double &sum) {
+    uint32_t cr[R];
+    uint32_t base[R], ev[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        cr[r] = 0;
+        if (MASKED || SUM) {
+            const int32_t ioff = tid + r * NT;
+            ev[r] = evals_of(tile0 + ioff, n, h);
+            base[r] = static_cast<uint32_t>(eo0 - ioff - 1);   // s - 1 of the stage's first object
+        }
+    }
+    if (MODE == MODE_I32_FAST && !MASKED && !SUM) {
+        // Unmasked fast form, i-outer over blocks of QB staged record pairs: each
+        // object's coefficients are the operand repeated by consecutive instructions.
+        constexpr int QB = 4;
+#pragma unroll 1
+        for (int q0 = 0; q0 < JS / 2; q0 += QB) {
+            f2 X[QB], Y[QB], Z[QB], B[QB];
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                const ulonglong2 p0 = st[2 * (q0 + q)];
+                const ulonglong2 p1 = st[2 * (q0 + q) + 1];
+                X[q] = p0.x;
+                Y[q] = p0.y;
+                Z[q] = p1.x;
+                B[q] = p1.y;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                f2 t[QB];
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_fma(s.a[r], X[q], B[q]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_fma(s.b[r], Y[q], t[q]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_fma(s.c[r], Z[q], t[q]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) t[q] = f2_add(t[q], s.d[r]);
+#pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    cr[r] += sign_lo(t[q]);
+                    cr[r] += sign_hi(t[q]);
+                }
+            }
+        }
+    } else {
+#pragma unroll(MASKED ? 1 : 2)
+    for (int q = 0; q < JS / 2; ++q) {
+        const ulonglong2 p0 = st[2 * q];
+        const ulonglong2 p1 = st[2 * q + 1];
+        uint32_t any = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            uint32_t h0, h1;
+            if (MODE == MODE_I32_FAST) {
+                const f2 v = fast_v(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1);
+                h0 = sign_lo(v);
+                h1 = sign_hi(v);
+            } else if (MODE == MODE_F32) {
+                float d2lo, d2hi;
+                f2 s2;
+                sphere_d2s2(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, d2lo, d2hi, s2);
+                h0 = d2lo <= f2_lo(s2) ? 1u : 0u;
+                h1 = d2hi <= f2_hi(s2) ? 1u : 0u;
+            } else {
+                h0 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x), f2_lo(p0.y),
+                             f2_lo(p1.x)) <= r2 ? 1u : 0u;
+                h1 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_hi(p0.x), f2_hi(p0.y),
+                             f2_hi(p1.x)) <= r2 ? 1u : 0u;
+            }
+            if (MASKED) {
+                const uint32_t s0 = base[r] + 2u * static_cast<uint32_t>(q);
+                h0 &= (s0 < ev[r]) ? 1u : 0u;
+                h1 &= (s0 + 1u < ev[r]) ? 1u : 0u;
+            }
+            cr[r] += h0;
+            cr[r] += h1;
+            if (SUM) any |= h0 | h1;
+        }
+        if (SUM && any) {
+#pragma unroll 1
+            for (int r = 0; r < R; ++r)
+                sum += pair_terms<MODE, NT>(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, eo0 + 2 * q,
+                                            tid + r * NT, ev[r], r2);
+        }
+    }
+    }
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) cnt += cr[r];
+    return cnt;
+}
+
+}  // namespace cc

@@ -67,7 +67,7 @@ def test_host_side_argument_errors(cc):
     assert L.cc_interaction_sum(ctypes.byref(f32), 10, 0, d, None, None) == cc.CC_ERR_INVALID_ARG
     h = ctypes.c_void_p()
     assert L.cc_plan_create(ctypes.byref(h), None, 0, 10) == cc.CC_ERR_INVALID_ARG
-    assert L.cc_plan_create(ctypes.byref(h), b'{"bands": [{"n_max": 10, "r": 3, "sc": 4}]}', 10, 10) \
+    assert L.cc_plan_create(ctypes.byref(h), b'{"bands": [{"n_max": 10, "r": 8, "sc": 4}]}', 10, 10) \
         == cc.CC_ERR_INVALID_ARG
     assert L.cc_plan_create(ctypes.byref(h), b'{"nothing": 1}', 10, 10) == cc.CC_ERR_INVALID_ARG
     assert L.cc_server_create(ctypes.byref(h), 0, 4) == cc.CC_ERR_INVALID_ARG

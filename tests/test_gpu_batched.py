@@ -113,9 +113,10 @@ def test_custom_band_table_same_results(cc):
     want = oracle.count_i32_sets(x, y, z, off, 9)
     tables = [
         None,
-        {"bands": [{"n_max": 16, "r": 1, "sc": 8}, {"n_max": 1000, "r": 8, "sc": 32},
+        {"bands": [{"n_max": 16, "r": 1, "sc": 1}, {"n_max": 1000, "r": 4, "sc": 2},
                    {"n_max": -1, "r": 2, "sc": 0}]},
-        {"bands": [{"n_max": -1, "r": 4, "sc": 100}]},
+        {"bands": [{"n_max": -1, "r": 4, "sc": 3}]},
+        {"bands": [{"n_max": -1, "r": 1, "sc": 0}]},
     ]
     for tb in tables:
         plan = cc.Plan(len(SIZES), len(x), json.dumps(tb) if tb else None)
