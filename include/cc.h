@@ -89,6 +89,13 @@ cc_status cc_count_pairs(const cc_points *p, int64_t n, uint32_t r2,
 cc_status cc_interaction_sum(const cc_points *p, int64_t n, uint32_t r2,
                              float *d_sum, unsigned long long *d_count, void *stream);
 
+/* The same count with the straightforward schedule the paper compares against
+ * (Section 5): each group of 1024 objects is tested against all later objects, so the
+ * work per group falls linearly along the set. Same records and inner loop as
+ * cc_count_pairs; provided to measure what the balanced cyclic schedule gains. */
+cc_status cc_count_pairs_straightforward(const cc_points *p, int64_t n, uint32_t r2,
+                                         unsigned long long *d_count, void *stream);
+
 /* Checks the integer range precondition on the device and WAITS for the answer
  * (synchronises the stream): CC_OK, or CC_ERR_RANGE when some axis spans more than
  * 32767. FP32 points always pass. */

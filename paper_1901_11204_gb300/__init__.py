@@ -61,6 +61,7 @@ _VP = ctypes.c_void_p
 _PTS = ctypes.POINTER(cc_points)
 _SIGS = {
     "cc_count_pairs": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
+    "cc_count_pairs_straightforward": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
     "cc_count_pairs_noalloc": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
     "cc_interaction_sum": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
     "cc_validate_points": ([_PTS, ctypes.c_int64, _VP], ctypes.c_int),
@@ -178,6 +179,18 @@ def count_pairs(x, y, z, r2: int = 0, r=None, out=None, stream=None):
     if out is None:
         out = torch.empty(1, dtype=torch.int64, device=x.device)
     _check(cc_count_pairs(pts, x.numel(), int(r2), out.data_ptr(), _stream_handle(stream)))
+    return out
+
+
+def count_pairs_straightforward(x, y, z, r2: int = 0, r=None, out=None, stream=None):
+    """Same count with the straightforward schedule of the paper's comparison (each group
+    of 1024 objects against all later ones); for measuring the balance effect."""
+    torch = _torch()
+    pts = make_points(x, y, z, r)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=x.device)
+    _check(lib().cc_count_pairs_straightforward(ctypes.byref(pts), x.numel(), int(r2), out.data_ptr(),
+                                                _stream_handle(stream)))
     return out
 
 

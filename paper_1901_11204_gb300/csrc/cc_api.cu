@@ -20,6 +20,9 @@ size_t single_ws_bytes(int64_t n, bool sum);
 cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
                          float *d_sum, void *ws, cudaStream_t stream);
 cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t stream);
+size_t straight_ws_bytes(int64_t n);
+cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count, void *ws,
+                           cudaStream_t stream);
 
 static thread_local std::string t_last_error;
 static std::atomic<uint64_t> g_wait_ns{2000000000ull};
@@ -238,6 +241,18 @@ cc_status cc_interaction_sum(const cc_points *p, int64_t n, uint32_t r2, float *
     st = workspace_for(s, single_ws_bytes(n, true), &ws);
     if (st != CC_OK) return st;
     return single_enqueue(p, n, r2, d_count, d_sum, ws, s);
+}
+
+cc_status cc_count_pairs_straightforward(const cc_points *p, int64_t n, uint32_t r2,
+                                        unsigned long long *d_count, void *stream) {
+    cc_status st = check_points(p, n);
+    if (st != CC_OK) return st;
+    if (!d_count || !aligned(d_count, 8)) return fail(CC_ERR_INVALID_ARG, "d_count is NULL or misaligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    st = workspace_for(s, std::max(straight_ws_bytes(n), sizeof(WsHeader)), &ws);
+    if (st != CC_OK) return st;
+    return straight_enqueue(p, n, r2, d_count, ws, s);
 }
 
 cc_status cc_stream_status(void *stream) {

@@ -25,8 +25,11 @@ __device__ __forceinline__ uint32_t sign_lo(f2 v) { return static_cast<uint32_t>
 __device__ __forceinline__ uint32_t sign_hi(f2 v) { return static_cast<uint32_t>(v >> 32) >> 31; }
 
 // Evaluations of object i (0 for i >= n): (n-1)/2, plus one for i < n/2 when n is even.
+// h < 0 selects the straightforward schedule used for comparison (Section 5): object i
+// evaluates every later object, n - 1 - i of them.
 __device__ __forceinline__ uint32_t evals_of(int64_t i, int64_t n, int32_t h) {
     if (i >= n) return 0u;
+    if (h < 0) return static_cast<uint32_t>(n - 1 - i);
     return static_cast<uint32_t>(h) + (((n & 1) == 0 && i < n / 2) ? 1u : 0u);
 }
 

@@ -538,6 +538,97 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_pairs_w(PairArgs A) {
 }
 
 // ---------------------------------------------------------------------------------------
+// straightforward schedule (the comparison kernel of Section 5): CTA b takes the group of
+// objects [b*G, (b+1)*G) and every warp its tile of 32*R of them against ALL later
+// objects, so tiles near the start carry much more work than tiles near the end. Same
+// records, same stage loop and same per-warp copy ring as the cyclic kernel; only the
+// schedule differs, which isolates the effect the paper measures.
+// ---------------------------------------------------------------------------------------
+
+template <int MODE, int R, int JS, int NS>
+__device__ __forceinline__ void straight_loop(const PairArgs &A, uint8_t *ring, uint64_t *full, int64_t tile,
+                                              int lane, unsigned long long &cnt64) {
+    constexpr int T = 32 * R;
+    constexpr uint32_t kBytes = JS * 16;
+    const int64_t a = tile * T;
+    if (a >= A.n) return;
+    const int64_t K = (A.n - a + JS - 1) / JS;   // stages from the tile start to the end
+    const int32_t ai_off = A.hdr->ai_off;
+    const uint32_t r2 = A.hdr->r2e;
+    int64_t issued = 0;
+    if (lane == 0) {
+        for (int64_t k = 0; k < K && k < NS; ++k) {
+            mbar_arrive_expect_tx(&full[k], kBytes);
+            bulk_g2s(ring + k * kBytes, A.E + ((a + k * JS) >> 1), kBytes, &full[k]);
+            ++issued;
+        }
+    }
+    __syncwarp();
+    IState<R> s;
+    load_i<32, R>(s, A, MODE, a, lane, ai_off);
+    double unused = 0.0;
+    bool timed_out = false;
+    int64_t k = 0;
+    for (; k < K; ++k) {
+        const int slot = static_cast<int>(k % NS);
+        if (!mbar_wait_bounded(&full[slot], static_cast<uint32_t>((k / NS) & 1), A.wait_ns)) {
+            if (lane == 0) atomicOr(&A.hdr->status, ST_TIMEOUT);
+            timed_out = true;
+            break;
+        }
+        const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(ring + slot * kBytes);
+        const int32_t eo0 = static_cast<int32_t>(k * JS);
+        const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (a + eo0 + JS - 1 <= A.n - 1);
+        cnt64 += full_stage ? stage_run<MODE, 32, R, JS, false, false>(s, st, eo0, lane, a, A.n, -1, r2, unused)
+                            : stage_run<MODE, 32, R, JS, true, false>(s, st, eo0, lane, a, A.n, -1, r2, unused);
+        __syncwarp();
+        if (lane == 0 && k + NS < K) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[slot], kBytes);
+            bulk_g2s(ring + slot * kBytes, A.E + ((a + (k + NS) * JS) >> 1), kBytes, &full[slot]);
+            ++issued;
+        }
+    }
+    if (timed_out && lane == 0) {
+        for (int64_t kk = k; kk < issued && kk < k + NS; ++kk)
+            (void)mbar_wait_bounded(&full[kk % NS], static_cast<uint32_t>((kk / NS) & 1), A.wait_ns);
+    }
+}
+
+template <int CLASS, int NW, int R, int JS, int NS>
+__global__ void __launch_bounds__(NW * 32, 1) k_pairs_straight(PairArgs A) {
+    using L = WarpSmem<NW, JS, NS>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    uint8_t *ring = smem + warp * L::kPerWarp;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kStages) + warp * NS;
+    unsigned long long *red_cnt = reinterpret_cast<unsigned long long *>(smem + L::kStages + L::kBars);
+    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
+    if (mode == MODE_RANGE_ERR) return;
+    if (lane == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(&full[i], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int64_t tile = static_cast<int64_t>(blockIdx.x) * NW + warp;
+    unsigned long long cnt64 = 0;
+    if (CLASS == CLASS_F32) straight_loop<MODE_F32, R, JS, NS>(A, ring, full, tile, lane, cnt64);
+    else if (mode == MODE_I32_FAST) straight_loop<MODE_I32_FAST, R, JS, NS>(A, ring, full, tile, lane, cnt64);
+    else straight_loop<MODE_I32_WIDE, R, JS, NS>(A, ring, full, tile, lane, cnt64);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt64 += __shfl_down_sync(0xFFFFFFFFu, cnt64, o);
+    if (lane == 0) red_cnt[warp] = cnt64;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long c = 0;
+        for (int i = 0; i < NW; ++i) c += red_cnt[i];
+        if (c && A.d_count) atomicAdd(A.d_count, c);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 
@@ -708,6 +799,66 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     const bool prof = profiling();
     if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.threads), args, L.smem, stream));
+    if (prof) profile_end(stream, e0, e1);
+    return CC_OK;
+}
+
+// Straightforward-schedule count (comparison path): same preparation, records padded to
+// whole stages, one CTA per group of 1024 objects.
+size_t straight_ws_bytes(int64_t n) {
+    constexpr int JS = 256;
+    // a tile may start mid-stage, so its last stage can end up to JS objects past n
+    const int64_t nrec = ((n + JS - 1) / JS + 1) * JS / 2;
+    return sizeof(WsHeader) + static_cast<size_t>(nrec) * sizeof(Rec) + 256;
+}
+
+cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count, void *ws,
+                           cudaStream_t stream) {
+    constexpr int NW = 8, R = 4, JS = 256, NS = 4;
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const bool f32 = p->dtype == CC_F32;
+    k_reset<<<1, 32, 0, stream>>>(hdr, f32 ? MODE_F32 : MODE_I32_FAST, d_count, nullptr);
+    CC_CUDA(cudaGetLastError());
+    if (n < 2) return CC_OK;
+    Rec *E = reinterpret_cast<Rec *>(reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader));
+    const int64_t nrec = ((n + JS - 1) / JS + 1) * JS / 2;   // see straight_ws_bytes
+    const int blocks = static_cast<int>(std::min<int64_t>((nrec + 255) / 256, sm_count() * 8));
+    if (!f32) {
+        const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+        k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
+                                                 static_cast<const int32_t *>(p->y),
+                                                 static_cast<const int32_t *>(p->z), n, r2, hdr, d_count);
+        k_fill_i32<<<blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
+                                               static_cast<const int32_t *>(p->y),
+                                               static_cast<const int32_t *>(p->z), n, nrec, E, hdr);
+    } else {
+        k_fill_f32<<<blocks, 256, 0, stream>>>(static_cast<const float *>(p->x), static_cast<const float *>(p->y),
+                                               static_cast<const float *>(p->z), p->r, n, nrec, E);
+    }
+    CC_CUDA(cudaGetLastError());
+    using L = WarpSmem<NW, JS, NS>;
+    const void *fn = f32 ? reinterpret_cast<const void *>(k_pairs_straight<CLASS_F32, NW, R, JS, NS>)
+                         : reinterpret_cast<const void *>(k_pairs_straight<CLASS_I32, NW, R, JS, NS>);
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[f32 ? 1 : 0]) {
+        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
+        attr_done[f32 ? 1 : 0] = true;
+    }
+    PairArgs A{};
+    A.E = E;
+    A.n = n;
+    A.units = 0;
+    A.K = 0;
+    A.h = -1;
+    A.hdr = hdr;
+    A.d_count = d_count;
+    A.wait_ns = wait_limit_ns();
+    void *args[] = {&A};
+    const int grid = static_cast<int>((n + NW * 32 * R - 1) / (NW * 32 * R));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool prof = profiling();
+    if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
+    CC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(NW * 32), args, L::kTotal, stream));
     if (prof) profile_end(stream, e0, e1);
     return CC_OK;
 }

@@ -239,3 +239,19 @@ def test_cfg3_full_size(cc):
     s, cnt = gpu_sum(cc, c["x"], c["y"], c["z"], 0, c["r"])
     assert cnt == want_c
     assert rel(s, want_s) <= SUM_RTOL
+
+
+@pytest.mark.parametrize("n", [2, 3, 100, 385, 1023, 1024, 1025, 5000, 65537])
+def test_straightforward_schedule_parity(cc, n):
+    """The comparison kernel (every object against all later ones) counts the same pairs."""
+    rng = np.random.default_rng(77 + n)
+    x, y, z = (rng.integers(0, 20, n).astype(np.int32) for _ in range(3))
+    t = dev(x, y, z)
+    got = cc.count_pairs_straightforward(*t, r2=4)
+    torch.cuda.synchronize()
+    assert cc.as_u64(got) == oracle.count_i32(x, y, z, 4)
+    xs, ys, zs, rs = synth.sphere_points(n, 5 + n, rmin=0.01, rmax=0.03)
+    tf = dev(xs, ys, zs, rs)
+    got = cc.count_pairs_straightforward(*tf[:3], r=tf[3])
+    torch.cuda.synchronize()
+    assert cc.as_u64(got) == oracle.count_f32(xs, ys, zs, rs)[0]
