@@ -126,6 +126,17 @@ def sphere_points(n: int, seed: int, rmin: float = 0.001, rmax: float = 0.004):
     return x, y, z, r
 
 
+def unit_spheres(n: int, box: float = 200.0, seed: int = SEED_BASE + 6):
+    """n FP32 spheres of diameter 1 (radius 0.5), centres uniform in [0, box)^3: the
+    shape of the paper's GPU experiment (random FP spheres of diameter 1, Section 5; the
+    box size is not stated there)."""
+    x = (uniform_f64(seed, 1, n) * box).astype(np.float32)
+    y = (uniform_f64(seed, 2, n) * box).astype(np.float32)
+    z = (uniform_f64(seed, 3, n) * box).astype(np.float32)
+    r = np.full(n, 0.5, dtype=np.float32)
+    return x, y, z, r
+
+
 def cfg1():
     seed = SEED_BASE + 1
     x, y, z = int_points(4096, 6, seed)
