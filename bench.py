@@ -356,6 +356,7 @@ def main():
         line["batched"] = bench_batched(cc, torch, dev)
         line["serving"] = bench_serving(cc, torch, dev, args.serving_queries)
         line["schedule_comparison"] = bench_schedules(cc, torch, dev)
+        line["linear_same_site"] = bench_linear(cc, torch, dev, peaks)
         line["cpu_baseline"] = cpu_baseline(sets)
 
     if world > 1:
@@ -400,6 +401,30 @@ def bench_f32(cc, torch, dev, sms, fmax, peak_src):
             "count": cc.as_u64(cnt), "sum": float(s.item()),
             "roofline_peak": peak, "count_frac": g_count / peak,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src}) / 10 FP32 ops per pair"}
+
+
+def bench_linear(cc, torch, dev, peaks):
+    """Algorithm 1 of Section 3 (linear-time same-site collisions) on the GPU, against the
+    pairwise kernel with r2 = 0 on the same input (both exact, same count)."""
+    out = {}
+    for n, bits in ((262144, 8), (16_777_216, 8)):
+        x, y, z = synth.int_points(n, bits, synth.SEED_BASE + 102)
+        t = [torch.from_numpy(a).to(dev) for a in (x, y, z)]
+        ms_lin = _time(lambda: cc.count_same_site(t[0], t[1], t[2]), 20, torch)
+        cnt = cc.as_u64(cc.count_same_site(t[0], t[1], t[2]))
+        rec = {"n": n, "box": f"[0,{1 << bits})^3", "linear_ms": ms_lin, "count": cnt,
+               "beads_per_s": n / (ms_lin * 1e-3),
+               # algorithmic bytes per bead: read 3 int32 coordinates (12 B), zero its site
+               # (4 B), atomic read-modify-write of the site (4 B read + 4 B write)
+               "algorithmic_gbs": 24.0 * n / (ms_lin * 1e-3) / 1e9,
+               "hbm_peak_gbs": peaks.get("hbm_gbs")}
+        if n <= 262144:
+            ms_pair = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r2=0), 5, torch)
+            rec["pairwise_ms"] = ms_pair
+            rec["speedup_linear_vs_pairwise"] = ms_pair / ms_lin
+            rec["pairwise_count_equal"] = cc.as_u64(cc.count_pairs(t[0], t[1], t[2], r2=0)) == cnt
+        out[f"n{n}"] = rec
+    return out
 
 
 def bench_schedules(cc, torch, dev, n=600_000):

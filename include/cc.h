@@ -96,6 +96,19 @@ cc_status cc_interaction_sum(const cc_points *p, int64_t n, uint32_t r2,
 cc_status cc_count_pairs_straightforward(const cc_points *p, int64_t n, uint32_t r2,
                                          unsigned long long *d_count, void *stream);
 
+/* ---- linear-time counts for integer beads (Section 3, Algorithms 1 and 2) ------------- */
+
+/* Algorithm 1 (countColls): the number of unordered pairs of beads on the same lattice
+ * site, in O(N) through a per-site count (dense over the bounding box when it is small,
+ * else a hash table in the stream's workspace). Equals cc_count_pairs with r2 = 0.
+ * CC_I32 only; per-axis spans up to 2^21 - 3 (else CC_ERR_RANGE via cc_stream_status and
+ * the count set to CC_COUNT_INVALID). */
+cc_status cc_count_same_site(const cc_points *p, int64_t n, unsigned long long *d_count, void *stream);
+
+/* Algorithm 2 (countContacts): the number of unordered pairs of beads on face-adjacent
+ * sites (squared distance exactly 1), in O(N). Same storage and limits as above. */
+cc_status cc_count_contacts(const cc_points *p, int64_t n, unsigned long long *d_count, void *stream);
+
 /* Checks the integer range precondition on the device and WAITS for the answer
  * (synchronises the stream): CC_OK, or CC_ERR_RANGE when some axis spans more than
  * 32767. FP32 points always pass. */

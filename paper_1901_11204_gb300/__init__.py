@@ -62,6 +62,8 @@ _PTS = ctypes.POINTER(cc_points)
 _SIGS = {
     "cc_count_pairs": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
     "cc_count_pairs_straightforward": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
+    "cc_count_same_site": ([_PTS, ctypes.c_int64, _VP, _VP], ctypes.c_int),
+    "cc_count_contacts": ([_PTS, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "cc_count_pairs_noalloc": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP], ctypes.c_int),
     "cc_interaction_sum": ([_PTS, ctypes.c_int64, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
     "cc_validate_points": ([_PTS, ctypes.c_int64, _VP], ctypes.c_int),
@@ -191,6 +193,26 @@ def count_pairs_straightforward(x, y, z, r2: int = 0, r=None, out=None, stream=N
         out = torch.empty(1, dtype=torch.int64, device=x.device)
     _check(lib().cc_count_pairs_straightforward(ctypes.byref(pts), x.numel(), int(r2), out.data_ptr(),
                                                 _stream_handle(stream)))
+    return out
+
+
+def count_same_site(x, y, z, out=None, stream=None):
+    """Algorithm 1 (Section 3): same-site bead pairs in linear time (int32 points)."""
+    torch = _torch()
+    pts = make_points(x, y, z)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=x.device)
+    _check(lib().cc_count_same_site(ctypes.byref(pts), x.numel(), out.data_ptr(), _stream_handle(stream)))
+    return out
+
+
+def count_contacts(x, y, z, out=None, stream=None):
+    """Algorithm 2 (Section 3): face-adjacent bead pairs in linear time (int32 points)."""
+    torch = _torch()
+    pts = make_points(x, y, z)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=x.device)
+    _check(lib().cc_count_contacts(ctypes.byref(pts), x.numel(), out.data_ptr(), _stream_handle(stream)))
     return out
 
 

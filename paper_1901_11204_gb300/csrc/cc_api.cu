@@ -21,6 +21,9 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
                          float *d_sum, void *ws, cudaStream_t stream);
 cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t stream);
 size_t straight_ws_bytes(int64_t n);
+size_t linear_ws_bytes(int64_t n);
+cc_status linear_enqueue(const cc_points *p, int64_t n, int contacts, unsigned long long *d_count, void *ws,
+                         cudaStream_t s);
 cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count, void *ws,
                            cudaStream_t stream);
 
@@ -253,6 +256,27 @@ cc_status cc_count_pairs_straightforward(const cc_points *p, int64_t n, uint32_t
     st = workspace_for(s, std::max(straight_ws_bytes(n), sizeof(WsHeader)), &ws);
     if (st != CC_OK) return st;
     return straight_enqueue(p, n, r2, d_count, ws, s);
+}
+
+static cc_status linear_call(const cc_points *p, int64_t n, int contacts, unsigned long long *d_count,
+                             void *stream) {
+    cc_status st = check_points(p, n);
+    if (st != CC_OK) return st;
+    if (p->dtype != CC_I32) return fail(CC_ERR_INVALID_ARG, "the linear-time counts need integer points");
+    if (!d_count || !aligned(d_count, 8)) return fail(CC_ERR_INVALID_ARG, "d_count is NULL or misaligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    st = workspace_for(s, linear_ws_bytes(n), &ws);
+    if (st != CC_OK) return st;
+    return linear_enqueue(p, n, contacts, d_count, ws, s);
+}
+
+cc_status cc_count_same_site(const cc_points *p, int64_t n, unsigned long long *d_count, void *stream) {
+    return linear_call(p, n, 0, d_count, stream);
+}
+
+cc_status cc_count_contacts(const cc_points *p, int64_t n, unsigned long long *d_count, void *stream) {
+    return linear_call(p, n, 1, d_count, stream);
 }
 
 cc_status cc_stream_status(void *stream) {

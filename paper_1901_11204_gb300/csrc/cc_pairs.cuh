@@ -43,22 +43,19 @@ __device__ __forceinline__ f2 fast_v(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0, ulon
     return f2_add(t, d);
 }
 
-// FP32 sphere predicate for two pairs, in the specified order and rounding. The
-// differences, the radius sum and its square are packed FP32x2 operations; the squares
-// of the differences and their sums use the scalar __fmul_rn/__fadd_rn intrinsics, which
-// are never contracted into a fused multiply-add (the packed forms were observed to be
-// contracted by the code generator, which would change the rounding).
-__device__ __forceinline__ void sphere_d2s2(f2 xi, f2 yi, f2 zi, f2 ri, ulonglong2 p0,
-                                            ulonglong2 p1, float &d2lo, float &d2hi, f2 &s2) {
-    const f2 dx = f2_sub(xi, p0.x);
-    const f2 dy = f2_sub(yi, p0.y);
-    const f2 dz = f2_sub(zi, p1.x);
-    const float x0 = f2_lo(dx), x1 = f2_hi(dx), y0 = f2_lo(dy), y1 = f2_hi(dy);
-    const float z0 = f2_lo(dz), z1 = f2_hi(dz);
-    d2lo = __fadd_rn(__fadd_rn(__fmul_rn(x0, x0), __fmul_rn(y0, y0)), __fmul_rn(z0, z0));
-    d2hi = __fadd_rn(__fadd_rn(__fmul_rn(x1, x1), __fmul_rn(y1, y1)), __fmul_rn(z1, z1));
-    const f2 sr = f2_add(ri, p1.y);
-    s2 = f2_mul(sr, sr);
+// FP32 sphere predicate for two pairs, in the specified order and rounding, written with
+// scalar __fadd_rn/__fsub_rn/__fmul_rn intrinsics: these are never contracted into a fused
+// multiply-add (packed multiply/add pairs were observed to be contracted by the code
+// generator, which would change the rounding), and reading the halves of the staged
+// register pairs directly avoids any packing/unpacking moves.
+__device__ __forceinline__ uint32_t sphere_hit(float xi, float yi, float zi, float ri, float xj, float yj,
+                                               float zj, float rj) {
+    const float dx = __fsub_rn(xi, xj);
+    const float dy = __fsub_rn(yi, yj);
+    const float dz = __fsub_rn(zi, zj);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    const float s = __fadd_rn(ri, rj);
+    return d2 <= __fmul_rn(s, s) ? 1u : 0u;
 }
 
 __device__ __forceinline__ uint32_t wide_d2(float xi, float yi, float zi, float xj, float yj, float zj) {
@@ -177,11 +174,9 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
                 h0 = sign_lo(v);
                 h1 = sign_hi(v);
             } else if (MODE == MODE_F32) {
-                float d2lo, d2hi;
-                f2 s2;
-                sphere_d2s2(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, d2lo, d2hi, s2);
-                h0 = d2lo <= f2_lo(s2) ? 1u : 0u;
-                h1 = d2hi <= f2_hi(s2) ? 1u : 0u;
+                const float xi = f2_lo(s.a[r]), yi = f2_lo(s.b[r]), zi = f2_lo(s.c[r]), ri = f2_lo(s.d[r]);
+                h0 = sphere_hit(xi, yi, zi, ri, f2_lo(p0.x), f2_lo(p0.y), f2_lo(p1.x), f2_lo(p1.y));
+                h1 = sphere_hit(xi, yi, zi, ri, f2_hi(p0.x), f2_hi(p0.y), f2_hi(p1.x), f2_hi(p1.y));
             } else {
                 h0 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x), f2_lo(p0.y),
                              f2_lo(p1.x)) <= r2 ? 1u : 0u;

@@ -687,16 +687,22 @@ static int large_variant() {
     static int v = -1;
     if (v < 0) {
         const char *e = getenv("CC_SINGLE_VARIANT");
-        v = e ? atoi(e) : 6;
-        if (v < 0 || v > 7) v = 6;
+        v = e ? atoi(e) : -2;
+        if (v < -2 || v > 7) v = -2;
     }
     return v;
 }
 
+// Measured best large-set shapes on GB300: 8 warps x 8 objects per lane for integer
+// points, 12 warps x 8 objects for FP32 spheres.
+template <int CLASS>
+static int large_default() { return CLASS == CLASS_F32 ? 4 : 6; }
+
 template <int CLASS, bool SUM>
 static cc_status pick_class(int64_t n, Launch &L) {
     if (n >= 65536) {
-        switch (large_variant()) {
+        const int v = large_variant() >= 0 ? large_variant() : large_default<CLASS>();
+        switch (v) {
             case 1: return get_launch<CLASS, 128, 8, 512, 6, SUM, 2>(L);
             case 2: return get_launch<CLASS, 256, 4, 512, 6, SUM, 2>(L);
             case 3: return get_launch<CLASS, 128, 4, 256, 8, SUM, 3>(L);
