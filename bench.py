@@ -180,6 +180,32 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
+KERNEL_SOURCES = ("paper_1901_11204_gb300/csrc/cc_single.cu", "paper_1901_11204_gb300/csrc/cc_pairs.cuh",
+                  "paper_1901_11204_gb300/csrc/cc_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the pair kernel from the committed ncu capture, or None
+    when the kernel sources changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "k_pairs_traffic.json")
+    if not os.path.exists(p):
+        return None, "no capture"
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_sha256") != kernel_source_hash():
+        return None, "kernel changed since the capture"
+    return float(d["dram_bytes_per_launch"]), d.get("workload", "")
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -289,10 +315,12 @@ def main():
     fmax = float(peaks.get("sm_max_mhz", 2070.0))
     peak = roofline_peak_int(sms, fmax) / 1e9
     achieved = tests_per_step * args.steps / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+    traffic, traffic_note = measured_traffic()
     roofline = {
-        "bound": "alu", "kernel": "k_pairs (single-set pair kernel)",
+        "bound": "alu", "kernel": "k_pairs_w (single-set pair kernel)",
         "achieved": achieved, "peak": peak, "unit": METRIC,
-        "frac": (achieved / peak) if achieved else None, "traffic": None,
+        "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+        "traffic_note": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch: {traffic_note}",
         "peak_basis": (f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src} sm_max_mhz) / "
                        "4 FP32-pipe ops per pair"),
         "kernel_share_of_step": (kern_ms / dev_ms) if dev_ms > 0 else None,

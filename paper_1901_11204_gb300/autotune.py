@@ -19,7 +19,7 @@ import statistics
 
 import numpy as np
 
-DEFAULT_BANDS = [(64, 1, 0), (512, 2, 0), (8192, 4, 16), (-1, 4, 64)]
+DEFAULT_BANDS = [(32, 0, 0), (64, 1, 8), (512, 2, 8), (8192, 4, 8), (-1, 4, 64)]
 R_CHOICES = (1, 2, 4)
 SC_CHOICES = (0, 2, 4, 8, 16, 32, 64)
 
@@ -62,8 +62,9 @@ def tune(points_per_band: int = 400_000, reps: int = 5, r_choices=R_CHOICES, sc_
         t = [torch.from_numpy(a).to(dev) for a in (x, y, z, off)]
         best = None
         ref = None
-        for r in r_choices:
-            for sc in sc_choices:
+        cands = [(0, 0)] if r0 == 0 else [(r, sc) for r in r_choices for sc in sc_choices]
+        for r, sc in cands:
+            if True:
                 cand = [list(b) for b in out_bands]
                 cand[bi] = [n_max, r, sc]
                 plan = Plan(len(off) - 1, len(x), _table(cand))

@@ -118,6 +118,7 @@ __host__ __device__ __forceinline__ int64_t chunks_of(const Band &b, int64_t n) 
 
 __host__ __device__ __forceinline__ int64_t items_of(const Band &b, int64_t n) {
     if (n < 2) return 0;
+    if (b.r == 0) return 1;   // warp-per-set shuffle path (sets of at most 32 objects)
     const int64_t T = tile_of(b);
     return ((n + T - 1) / T) * chunks_of(b, n);
 }
@@ -381,10 +382,96 @@ __device__ __forceinline__ void run_item_mode(const SetDesc &d, const SetAux &x,
     else run_item<MODE_I32_WIDE, R, SUM>(d, x, b, local, slot, c, s);
 }
 
+// Sets of at most 32 objects: lane l holds object l and, at step s, gets its partner
+// (l + s) mod n from another lane by shuffles: the proposed algorithm with one object per
+// lane, exactly evals(i) tests per object and no staging or masks.
+template <int MODE, bool SUM>
+__device__ void run_tiny(const SetDesc &d, const SetAux &x, unsigned long long &cnt_out, double &sum_out) {
+    const int lane = threadIdx.x & 31;
+    const int32_t n = static_cast<int32_t>(d.n);
+    const int32_t h = (n - 1) / 2;
+    const bool even = (n & 1) == 0;
+    const bool valid = lane < n;
+    const int32_t i = valid ? lane : 0;
+    float xi, yi, zi, wi;   // own object, in the staged-record convention
+    if (MODE == MODE_I32_FAST) {
+        const int32_t a = static_cast<const int32_t *>(d.x)[i] - x.cx;
+        const int32_t b = static_cast<const int32_t *>(d.y)[i] - x.cy;
+        const int32_t c = static_cast<const int32_t *>(d.z)[i] - x.cz;
+        xi = static_cast<float>(a);
+        yi = static_cast<float>(b);
+        zi = static_cast<float>(c);
+        wi = static_cast<float>(a * a + b * b + c * c);
+    } else if (MODE == MODE_F32) {
+        xi = static_cast<const float *>(d.x)[i];
+        yi = static_cast<const float *>(d.y)[i];
+        zi = static_cast<const float *>(d.z)[i];
+        wi = d.r[i];
+    } else {
+        xi = __int_as_float(static_cast<const int32_t *>(d.x)[i]);
+        yi = __int_as_float(static_cast<const int32_t *>(d.y)[i]);
+        zi = __int_as_float(static_cast<const int32_t *>(d.z)[i]);
+        wi = 0.0f;
+    }
+    const float ax = -2.0f * xi, ay = -2.0f * yi, az = -2.0f * zi;
+    const float di = static_cast<float>(static_cast<int32_t>(wi) - x.ai_off);
+    const int32_t steps = h + (even ? 1 : 0);
+    uint32_t cnt = 0;
+    double sum = 0.0;
+    int32_t src = lane + 1 < n ? lane + 1 : lane + 1 - n;
+    for (int32_t s = 1; s <= steps; ++s) {
+        const float xj = __shfl_sync(0xFFFFFFFFu, xi, src);
+        const float yj = __shfl_sync(0xFFFFFFFFu, yi, src);
+        const float zj = __shfl_sync(0xFFFFFFFFu, zi, src);
+        const float wj = __shfl_sync(0xFFFFFFFFu, wi, src);
+        const bool ok = valid && (s <= h || lane < n / 2);
+        uint32_t hit;
+        uint32_t d2i = 0;
+        if (MODE == MODE_I32_FAST) {
+            const float v = __fadd_rn(__fmaf_rn(az, zj, __fmaf_rn(ay, yj, __fmaf_rn(ax, xj, wj))), di);
+            hit = __float_as_uint(v) >> 31;
+            if (SUM) {
+                const int32_t ex = static_cast<int32_t>(xi) - static_cast<int32_t>(xj);
+                const int32_t ey = static_cast<int32_t>(yi) - static_cast<int32_t>(yj);
+                const int32_t ez = static_cast<int32_t>(zi) - static_cast<int32_t>(zj);
+                d2i = static_cast<uint32_t>(ex * ex + ey * ey + ez * ez);
+            }
+        } else if (MODE == MODE_F32) {
+            hit = sphere_hit(xi, yi, zi, wi, xj, yj, zj, wj);
+        } else {
+            d2i = wide_d2(xi, yi, zi, xj, yj, zj);
+            hit = d2i <= x.r2e ? 1u : 0u;
+        }
+        hit = ok ? hit : 0u;
+        cnt += hit;
+        if (SUM && hit) {
+            if (MODE == MODE_F32) {
+                const float dx = __fsub_rn(xi, xj), dy = __fsub_rn(yi, yj), dz = __fsub_rn(zi, zj);
+                sum += term_from_d2f(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+            } else {
+                sum += term_from_d2f(static_cast<float>(d2i));
+            }
+        }
+        src = src + 1 < n ? src + 1 : 0;
+    }
+    unsigned long long c64 = cnt;
+    for (int o = 16; o > 0; o >>= 1) {
+        c64 += __shfl_down_sync(0xFFFFFFFFu, c64, o);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    }
+    cnt_out = c64;
+    sum_out = sum;
+}
+
 template <bool SUM>
 __device__ __forceinline__ void run_item_r(const SetDesc &d, const SetAux &x, const Band &b, int32_t local,
                                            Rec *slot, unsigned long long &c, double &s) {
     switch (b.r) {
+        case 0:
+            if (x.mode == MODE_I32_FAST) run_tiny<MODE_I32_FAST, SUM>(d, x, c, s);
+            else if (x.mode == MODE_F32) run_tiny<MODE_F32, SUM>(d, x, c, s);
+            else run_tiny<MODE_I32_WIDE, SUM>(d, x, c, s);
+            break;
         case 1: run_item_mode<1, SUM>(d, x, b, local, slot, c, s); break;
         case 2: run_item_mode<2, SUM>(d, x, b, local, slot, c, s); break;
         default: run_item_mode<4, SUM>(d, x, b, local, slot, c, s); break;
@@ -458,16 +545,18 @@ __global__ void k_b_finish(const BatchParams *__restrict__ P, const int32_t *cnt
 
 static BandTable default_bands() {
     BandTable t{};
-    t.count = 4;
-    t.band[0] = Band{64, 1, 0};
-    t.band[1] = Band{512, 2, 0};
-    t.band[2] = Band{8192, 4, 16};
-    t.band[3] = Band{INT64_MAX, 4, 64};
+    t.count = 5;
+    t.band[0] = Band{32, 0, 0};
+    t.band[1] = Band{64, 1, 8};
+    t.band[2] = Band{512, 2, 8};
+    t.band[3] = Band{8192, 4, 8};
+    t.band[4] = Band{INT64_MAX, 4, 64};
     return t;
 }
 
 // Minimal parser for {"bands": [{"n_max": N, "r": R, "sc": S}, ...]} (n_max -1 = no limit;
-// r objects per lane in {1, 2, 4}; sc stages of 64 objects per work item, 0 = all).
+// r objects per lane in {1, 2, 4}, or 0 for the one-object-per-lane shuffle path of sets
+// of at most 32 objects; sc stages of 64 objects per work item, 0 = all).
 static bool parse_bands(const char *json, BandTable &out, std::string &err) {
     BandTable t{};
     const char *p = strstr(json, "\"bands\"");
@@ -493,7 +582,14 @@ static bool parse_bands(const char *json, BandTable &out, std::string &err) {
         long long nmax = 0, r = 0, sc = 0;
         if (!field("n_max", nmax) || !field("r", r) || !field("sc", sc)) { err = "band needs n_max, r, sc"; return false; }
         if (t.count >= kMaxBands) { err = "too many bands"; return false; }
-        if (!(r == 1 || r == 2 || r == 4) || sc < 0) { err = "r must be 1, 2 or 4 and sc >= 0"; return false; }
+        if (!(r == 0 || r == 1 || r == 2 || r == 4) || sc < 0) {
+            err = "r must be 0, 1, 2 or 4 and sc >= 0";
+            return false;
+        }
+        if (r == 0 && nmax > 32) {
+            err = "r = 0 (one object per lane) needs n_max <= 32";
+            return false;
+        }
         t.band[t.count++] = Band{nmax < 0 ? INT64_MAX : nmax, static_cast<int32_t>(r), static_cast<int32_t>(sc)};
         p = cb + 1;
     }

@@ -10,6 +10,7 @@
 // soon as a lane frees up. Results carry host steady-clock timestamps of arrival and of
 // completion.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -114,7 +115,15 @@ static size_t req_scratch(int64_t n) {
     return 256 + static_cast<size_t>(n) * 2;
 }
 
+// NVTX ranges mark batch formation/launch and harvesting on the scheduler thread (visible
+// in Nsight Systems timelines; no cost when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 static void harvest(cc_server *S, Lane &L) {
+    NvtxRange range("cc_server harvest");
     const double t = now_s();
     std::lock_guard<std::mutex> lk(S->mu);
     for (size_t k = 0; k < L.batch.size(); ++k) {
@@ -143,6 +152,7 @@ static void harvest(cc_server *S, Lane &L) {
 
 // Forms and launches one batch on lane L (called with S->mu NOT held).
 static bool launch(cc_server *S, Lane &L) {
+    NvtxRange range("cc_server form+launch batch");
     std::vector<Req> batch;
     size_t scratch = 0;
     int64_t points = 0;

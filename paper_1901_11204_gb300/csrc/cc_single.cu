@@ -688,15 +688,15 @@ static int large_variant() {
     if (v < 0) {
         const char *e = getenv("CC_SINGLE_VARIANT");
         v = e ? atoi(e) : -2;
-        if (v < -2 || v > 7) v = -2;
+        if (v < -2 || v > 10) v = -2;
     }
     return v;
 }
 
-// Measured best large-set shapes on GB300: 8 warps x 8 objects per lane for integer
-// points, 12 warps x 8 objects for FP32 spheres.
+// Measured best large-set shape on GB300 for both classes: 12 warps x 6 objects per lane
+// (160 registers, 3 warps per SMSP), 256-object stages, 4-deep rings.
 template <int CLASS>
-static int large_default() { return CLASS == CLASS_F32 ? 4 : 6; }
+static int large_default() { return 9; }
 
 template <int CLASS, bool SUM>
 static cc_status pick_class(int64_t n, Launch &L) {
@@ -710,6 +710,9 @@ static cc_status pick_class(int64_t n, Launch &L) {
             case 5: return get_launch_w<CLASS, 16, 4, 128, 4, SUM, 1>(L);
             case 6: return get_launch_w<CLASS, 8, 8, 256, 4, SUM, 1>(L);
             case 7: return get_launch_w<CLASS, 16, 4, 256, 3, SUM, 1>(L);
+            case 8: return get_launch_w<CLASS, 8, 8, 256, 4, SUM, 2>(L);
+            case 9: return get_launch_w<CLASS, 12, 6, 256, 4, SUM, 1>(L);
+            case 10: return get_launch_w<CLASS, 8, 8, 512, 3, SUM, 1>(L);
             default: return get_launch<CLASS, 256, 8, 512, 6, SUM, 1>(L);
         }
     }

@@ -117,6 +117,7 @@ def test_custom_band_table_same_results(cc):
                    {"n_max": -1, "r": 2, "sc": 0}]},
         {"bands": [{"n_max": -1, "r": 4, "sc": 3}]},
         {"bands": [{"n_max": -1, "r": 1, "sc": 0}]},
+        {"bands": [{"n_max": 32, "r": 0, "sc": 0}, {"n_max": -1, "r": 2, "sc": 5}]},
     ]
     for tb in tables:
         plan = cc.Plan(len(SIZES), len(x), json.dumps(tb) if tb else None)
