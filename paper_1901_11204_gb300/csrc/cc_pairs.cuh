@@ -108,7 +108,7 @@ __device__ __noinline__ double pair_terms(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0,
 
 // One stage for one consumer thread: JS staged objects against the thread's R objects.
 // MASKED applies the cyclic schedule's validity per pair: s = e - i must be in 1..evals(i).
-// With SUM, a record group that produced a hit is re-walked for its interaction terms.
+// With SUM, record pairs that produced a hit are re-walked for their interaction terms.
 // Each object slot r has its own counter so that the accumulations do not form one long
 // dependency chain.
 template <int MODE, int NT, int R, int JS, bool MASKED, bool SUM>
@@ -161,8 +161,15 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
             }
         }
     } else {
+    // Groups of up to 64 record pairs; with SUM, the groups that produced a hit are
+    // marked in a 64-bit mask and their interaction terms are added after the group, so
+    // the rarely taken term code stays out of the inner loop.
+#pragma unroll 1
+    for (int g0 = 0; g0 < JS / 2; g0 += 64) {
+    uint64_t hitmask = 0;
+    const int gend = (g0 + 64 < JS / 2) ? g0 + 64 : JS / 2;
 #pragma unroll(MASKED ? 1 : 2)
-    for (int q = 0; q < JS / 2; ++q) {
+    for (int q = g0; q < gend; ++q) {
         const ulonglong2 p0 = st[2 * q];
         const ulonglong2 p1 = st[2 * q + 1];
         uint32_t any = 0;
@@ -192,12 +199,21 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
             cr[r] += h1;
             if (SUM) any |= h0 | h1;
         }
-        if (SUM && any) {
+        if (SUM) hitmask |= static_cast<uint64_t>(any) << (q - g0);
+    }
+    if (SUM) {
+        while (hitmask) {
+            const int b = __ffsll(static_cast<long long>(hitmask)) - 1;
+            hitmask &= hitmask - 1;
+            const int q = g0 + b;
+            const ulonglong2 p0 = st[2 * q];
+            const ulonglong2 p1 = st[2 * q + 1];
 #pragma unroll 1
             for (int r = 0; r < R; ++r)
                 sum += pair_terms<MODE, NT>(s.a[r], s.b[r], s.c[r], s.d[r], p0, p1, eo0 + 2 * q,
                                             tid + r * NT, ev[r], r2);
         }
+    }
     }
     }
     uint32_t cnt = 0;

@@ -29,6 +29,10 @@
 #include "cc_internal.cuh"
 #include "cc_pairs.cuh"
 
+#ifndef CC_OPAQUE_ISTATE
+#define CC_OPAQUE_ISTATE 1
+#endif
+
 namespace cc {
 
 // ---------------------------------------------------------------------------------------
@@ -227,6 +231,15 @@ __device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t 
             s.c[r] = f2_dup(z);
             s.d[r] = 0;
         }
+#if CC_OPAQUE_ISTATE
+        // Route the duplicated operands through a shuffle so that the code generator
+        // keeps them as genuine register pairs instead of rebuilding the pair before
+        // every packed instruction.
+        s.a[r] = __shfl_sync(0xFFFFFFFFu, s.a[r], tid & 31);
+        s.b[r] = __shfl_sync(0xFFFFFFFFu, s.b[r], tid & 31);
+        s.c[r] = __shfl_sync(0xFFFFFFFFu, s.c[r], tid & 31);
+        s.d[r] = __shfl_sync(0xFFFFFFFFu, s.d[r], tid & 31);
+#endif
     }
 }
 
@@ -693,10 +706,11 @@ static int large_variant() {
     return v;
 }
 
-// Measured best large-set shape on GB300 for both classes: 12 warps x 6 objects per lane
-// (160 registers, 3 warps per SMSP), 256-object stages, 4-deep rings.
+// Measured best large-set shape on GB300 for both classes: 12 warps x 8 objects per lane,
+// 256-object stages, 4-deep rings (with the object state kept in genuine register
+// pairs, see load_i).
 template <int CLASS>
-static int large_default() { return 9; }
+static int large_default() { return 4; }
 
 template <int CLASS, bool SUM>
 static cc_status pick_class(int64_t n, Launch &L) {
