@@ -125,6 +125,25 @@ cc_status cc_release(void *stream);
  * it since the previous cc_stream_status(), and clears it. */
 cc_status cc_stream_status(void *stream);
 
+/* Diagnostic: synchronises `stream` and writes to *mode which pair kernel the device
+ * chose for the last cc_count_pairs / cc_interaction_sum call on it:
+ *   CC_MODE_FP32_EXACT   integer points, expanded-square form exact in FP32 (FP32 pipe)
+ *   CC_MODE_INT_WIDE     integer points, int32 difference form (spans up to 32767)
+ *   CC_MODE_RANGE_ERROR  span above 32767: nothing was counted
+ *   CC_MODE_FP32_SPHERES FP32 spheres
+ *   CC_MODE_TENSOR       integer points, the same exact form as a TF32 tensor-core
+ *                        contraction (counts only, n >= 16384, and only while the
+ *                        absolute values of its eight terms sum to less than 2^24)
+ * CC_ERR_NOT_FOUND when no call has run on `stream` yet. */
+enum {
+    CC_MODE_FP32_EXACT = 0,
+    CC_MODE_INT_WIDE = 1,
+    CC_MODE_RANGE_ERROR = 2,
+    CC_MODE_FP32_SPHERES = 3,
+    CC_MODE_TENSOR = 4
+};
+cc_status cc_stream_mode(void *stream, int32_t *mode);
+
 /* Same result as cc_count_pairs, for callers that must not allocate device memory while
  * they run: code recording into a CUDA graph, engines whose single allocator forbids side
  * allocations, services with a fixed memory budget that must not fail mid-run on an

@@ -70,6 +70,7 @@ _SIGS = {
     "cc_reserve": ([ctypes.c_int64, _VP], ctypes.c_int),
     "cc_release": ([_VP], ctypes.c_int),
     "cc_stream_status": ([_VP], ctypes.c_int),
+    "cc_stream_mode": ([_VP, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "cc_plan_create": ([ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
     "cc_plan_destroy": ([_VP], None),
     "cc_count_pairs_batched": ([_VP, _PTS, _VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
@@ -238,6 +239,17 @@ def validate_points(x, y, z, r=None, stream=None) -> int:
 
 def stream_status(stream=None) -> int:
     return cc_stream_status(_stream_handle(stream))
+
+
+# Pair kernel chosen by the device for the last single-set call on a stream
+# (cc_stream_mode): the CC_MODE_* values of cc.h.
+MODE_FP32_EXACT, MODE_INT_WIDE, MODE_RANGE_ERROR, MODE_FP32_SPHERES, MODE_TENSOR = 0, 1, 2, 3, 4
+
+
+def stream_mode(stream=None) -> int:
+    m = ctypes.c_int32(-1)
+    _check(lib().cc_stream_mode(_stream_handle(stream), ctypes.byref(m)))
+    return int(m.value)
 
 
 def reserve(max_n: int, stream=None):

@@ -16,9 +16,9 @@
 
 namespace cc {
 
-size_t single_ws_bytes(int64_t n, bool sum);
+size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc);
 cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
-                         float *d_sum, void *ws, cudaStream_t stream);
+                         float *d_sum, void *ws, cudaStream_t stream, bool allow_tc);
 cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t stream);
 size_t straight_ws_bytes(int64_t n);
 size_t linear_ws_bytes(int64_t n);
@@ -205,7 +205,7 @@ cc_status cc_profile_read(double *total_ms, int64_t *launches) {
 
 cc_status cc_reserve(int64_t max_n, void *stream) {
     if (max_n < 0) return fail(CC_ERR_INVALID_ARG, "max_n < 0");
-    size_t b = std::max(single_ws_bytes(max_n, true), single_ws_bytes(max_n, false));
+    size_t b = std::max(single_ws_bytes(max_n, true, true), single_ws_bytes(max_n, false, true));
     void *ws = nullptr;
     return workspace_for(static_cast<cudaStream_t>(stream), b, &ws);
 }
@@ -227,9 +227,9 @@ cc_status cc_count_pairs(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     if (!aligned(d_count, 8)) return fail(CC_ERR_INVALID_ARG, "d_count must be 8-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void *ws = nullptr;
-    st = workspace_for(s, single_ws_bytes(n, false), &ws);
+    st = workspace_for(s, single_ws_bytes(n, false, true), &ws);
     if (st != CC_OK) return st;
-    return single_enqueue(p, n, r2, d_count, nullptr, ws, s);
+    return single_enqueue(p, n, r2, d_count, nullptr, ws, s, true);
 }
 
 cc_status cc_interaction_sum(const cc_points *p, int64_t n, uint32_t r2, float *d_sum,
@@ -241,9 +241,9 @@ cc_status cc_interaction_sum(const cc_points *p, int64_t n, uint32_t r2, float *
         return fail(CC_ERR_INVALID_ARG, "misaligned output pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void *ws = nullptr;
-    st = workspace_for(s, single_ws_bytes(n, true), &ws);
+    st = workspace_for(s, single_ws_bytes(n, true, true), &ws);
     if (st != CC_OK) return st;
-    return single_enqueue(p, n, r2, d_count, d_sum, ws, s);
+    return single_enqueue(p, n, r2, d_count, d_sum, ws, s, true);
 }
 
 cc_status cc_count_pairs_straightforward(const cc_points *p, int64_t n, uint32_t r2,
@@ -298,6 +298,23 @@ cc_status cc_stream_status(void *stream) {
     CC_CUDA(cudaStreamSynchronize(s));
     if (status & ST_TIMEOUT) return fail(CC_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (status & ST_RANGE) return fail(CC_ERR_RANGE, "integer coordinate span above 32767 on some axis");
+    return CC_OK;
+}
+
+cc_status cc_stream_mode(void *stream, int32_t *mode) {
+    if (!mode) return fail(CC_ERR_INVALID_ARG, "mode is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws.find(s);
+        if (it == g_ws.end() || !it->second.ptr) return fail(CC_ERR_NOT_FOUND, "no call has run on this stream");
+        ws = it->second.ptr;
+    }
+    int32_t m = -1;
+    CC_CUDA(cudaMemcpyAsync(&m, &reinterpret_cast<WsHeader *>(ws)->mode, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CC_CUDA(cudaStreamSynchronize(s));
+    *mode = m;
     return CC_OK;
 }
 

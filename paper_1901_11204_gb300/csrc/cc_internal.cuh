@@ -46,7 +46,8 @@ enum : int32_t {
     MODE_I32_FAST = 0,   // centred int coordinates as exact FP32, expanded-square form
     MODE_I32_WIDE = 1,   // int32 difference form (spans up to 32767)
     MODE_RANGE_ERR = 2,  // span above 32767: nothing is counted
-    MODE_F32 = 3         // FP32 spheres
+    MODE_F32 = 3,        // FP32 spheres
+    MODE_I32_TC = 4      // fast exact form as a TF32 tensor-core contraction (count only)
 };
 
 // Workspace header: lives at the start of each stream's scratch buffer.
@@ -63,11 +64,24 @@ struct WsHeader {
     uint32_t pad[17];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
+static_assert(MODE_I32_FAST == CC_MODE_FP32_EXACT && MODE_I32_WIDE == CC_MODE_INT_WIDE &&
+                  MODE_RANGE_ERR == CC_MODE_RANGE_ERROR && MODE_F32 == CC_MODE_FP32_SPHERES &&
+                  MODE_I32_TC == CC_MODE_TENSOR,
+              "device modes are the public CC_MODE_* values");
 
 // Largest half-span m = ceil(span/2) for which the FP32 expanded-square form is exact:
 // every partial |n_j - 2 p_i.p_j| <= 9 m^2 and |n_i - r2e - 1| <= 12 m^2 + 1 stay
 // below 2^24.
 constexpr int32_t FAST_MAX_HALF_SPAN = 1182;
+// Tensor-core form: exact when the absolute values of the eight TF32 terms of
+// d^2 - r2e - 1 sum to less than 2^24 (every partial sum is then an exact FP32 integer):
+//   6 m^2 (three -2 p_i p_j products) + 3 m^2 (|p_j|^2 as two digits)
+//   + |n_i - r2e - 1| (<= max(r2e + 1, 3 m^2)) + 2^22 + 2^11 (slack of the balanced digits).
+__host__ __device__ inline bool tc_exact(int64_t m, int64_t r2e) {
+    const int64_t m2 = m * m;
+    const int64_t c = (r2e + 1) > 3 * m2 ? (r2e + 1) : 3 * m2;
+    return 9 * m2 + c + (int64_t{1} << 22) + 2048 < (int64_t{1} << 24);
+}
 // Integer precondition: per-axis span such that the squared distance fits in u32.
 constexpr int32_t WIDE_MAX_SPAN = 32767;
 
@@ -138,6 +152,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     const uint64_t t0 = globaltimer_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity, 200000u)) return true;
+        if (abort && *abort) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Non-blocking test of phase `parity` (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Like mbar_wait_bounded, but polls without suspending: for waits on the critical path
+// of a short pipeline, where the wake-up latency of a suspended wait would dominate.
+// The global timer and the abort flag are read every 256 polls.
+__device__ __forceinline__ bool mbar_spin_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                                  const volatile int *abort = nullptr) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int k = 0; k < 256; ++k)
+            if (mbar_test_wait(bar, parity)) return true;
         if (abort && *abort) return false;
         if (globaltimer_ns() - t0 > limit_ns) return false;
     }

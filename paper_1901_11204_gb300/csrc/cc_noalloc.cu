@@ -22,9 +22,9 @@
 
 namespace cc {
 
-size_t single_ws_bytes(int64_t n, bool sum);
+size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc);
 cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
-                         float *d_sum, void *ws, cudaStream_t stream);
+                         float *d_sum, void *ws, cudaStream_t stream, bool allow_tc);
 
 // 8 MiB of scratch: enough for sets of about 340 thousand objects.
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
@@ -61,7 +61,7 @@ static int64_t noalloc_max_n() {
     int64_t lo = 1, hi = int64_t(1) << 26;
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;
-        const size_t b = single_ws_bytes(mid, false);
+        const size_t b = single_ws_bytes(mid, false, false);
         if (b != 0 && b <= kNoAllocScratchBytes) lo = mid;
         else hi = mid - 1;
     }
@@ -95,7 +95,9 @@ cc_status cc_count_pairs_noalloc(const cc_points *p, int64_t n, uint32_t r2, uns
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the header's status word keeps the previous call's bits: start each call from zero
     CC_CUDA(cudaMemsetAsync(&reinterpret_cast<WsHeader *>(ws)->status, 0, sizeof(uint32_t), s));
-    return single_enqueue(p, n, r2, d_count, nullptr, ws, s);
+    // the tensor-core operands would need about three times the scratch: the static
+    // array serves the FP32-pipe kernel only
+    return single_enqueue(p, n, r2, d_count, nullptr, ws, s, false);
 }
 
 }  // extern "C"

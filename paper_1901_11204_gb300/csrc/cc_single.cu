@@ -35,6 +35,15 @@
 
 namespace cc {
 
+// tensor-core path (cc_tc.cu)
+size_t tc_region_bytes(int64_t n);
+bool tc_enabled();
+cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream);
+cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
+                           cudaStream_t stream);
+// Smallest set for which counts take the tensor-core kernel.
+constexpr int64_t TC_MIN_N = 16384;
+
 // ---------------------------------------------------------------------------------------
 // preparation kernels
 // ---------------------------------------------------------------------------------------
@@ -59,7 +68,7 @@ __global__ void k_reset(WsHeader *h, int32_t mode, unsigned long long *d_count, 
 // execution mode, the integer centre and the clamped r2 (no spin: last-block ticket).
 __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
                          const int32_t *__restrict__ z, int64_t n, uint32_t r2, WsHeader *h,
-                         unsigned long long *d_count) {
+                         unsigned long long *d_count, int32_t allow_tc) {
     uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
     uint32_t mx[3] = {0u, 0u, 0u};
     const int32_t *c[3] = {x, y, z};
@@ -117,6 +126,7 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
         mode = MODE_I32_WIDE;
     }
     int64_t r2e = static_cast<int64_t>(r2) < dmax ? static_cast<int64_t>(r2) : dmax;
+    if (mode == MODE_I32_FAST && allow_tc && tc_exact(m, r2e)) mode = MODE_I32_TC;
     h->r2e = static_cast<uint32_t>(r2e);
     h->ai_off = static_cast<int32_t>(r2e + 1);
     h->mode = mode;
@@ -128,7 +138,7 @@ __global__ void k_fill_i32(const int32_t *__restrict__ x, const int32_t *__restr
                            const int32_t *__restrict__ z, int64_t n, int64_t nrec,
                            Rec *__restrict__ E, const WsHeader *__restrict__ h) {
     const int32_t mode = h->mode;
-    if (mode == MODE_RANGE_ERR) return;
+    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC) return;
     const int32_t cx = h->cx, cy = h->cy, cz = h->cz;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrec;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) k_pairs(PairArgs A) {
     const int tid = threadIdx.x;
     const int warp = tid / 32;
     const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
-    if (mode == MODE_RANGE_ERR) return;   // count already marked invalid
+    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC) return;   // invalid, or the tensor-core kernel runs
 
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) {
@@ -494,7 +504,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_pairs_w(PairArgs A) {
     double *red_sum = reinterpret_cast<double *>(red_cnt + (NW + 1));
 
     const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
-    if (mode == MODE_RANGE_ERR) return;   // count already marked invalid
+    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC) return;   // invalid, or the tensor-core kernel runs
 
     if (lane == 0) {
         for (int i = 0; i < NS; ++i) mbar_init(&full[i], 1);
@@ -760,19 +770,27 @@ static cc_status pick_launch(int64_t n, bool f32, bool sum, Launch &L) {
     return sum ? pick_class<CLASS_I32, true>(n, L) : pick_class<CLASS_I32, false>(n, L);
 }
 
-size_t single_ws_bytes(int64_t n, bool sum) {
+static bool use_tc(int64_t n, bool sum, bool allow_tc) {
+    return allow_tc && !sum && n >= TC_MIN_N && tc_enabled();
+}
+
+// Workspace layout: WsHeader | region | double partial[grid], where the region holds
+// either the extended record array or (tensor-core mode) the two operand arrays.
+size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc) {
     if (n < 2) return sizeof(WsHeader);
     // the geometry depends only on the tile shape, which is the same for both classes
     Launch L;
     if (pick_launch(n, false, sum, L) != CC_OK) return 0;
     Geometry g = geometry(n, L);
-    return sizeof(WsHeader) + static_cast<size_t>(g.nrec) * sizeof(Rec) +
-           static_cast<size_t>(g.grid) * sizeof(double) + 256;
+    size_t region = static_cast<size_t>(g.nrec) * sizeof(Rec);
+    if (use_tc(n, sum, allow_tc)) region = std::max(region, tc_region_bytes(n));
+    region = (region + 255) & ~static_cast<size_t>(255);
+    return sizeof(WsHeader) + region + static_cast<size_t>(g.grid) * sizeof(double) + 256;
 }
 
 // Enqueues the whole single-set path on `stream` using workspace `ws` (>= single_ws_bytes).
 cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
-                         float *d_sum, void *ws, cudaStream_t stream) {
+                         float *d_sum, void *ws, cudaStream_t stream, bool allow_tc) {
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const bool f32 = p->dtype == CC_F32;
     k_reset<<<1, 32, 0, stream>>>(hdr, f32 ? MODE_F32 : MODE_I32_FAST, d_count, d_sum);
@@ -783,8 +801,13 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     cc_status st = pick_launch(n, f32, sum, L);
     if (st != CC_OK) return st;
     Geometry g = geometry(n, L);
-    Rec *E = reinterpret_cast<Rec *>(reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader));
-    double *partial = reinterpret_cast<double *>(E + g.nrec);
+    const bool tc = !f32 && use_tc(n, sum, allow_tc);
+    uint8_t *region = reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader);
+    size_t region_bytes = static_cast<size_t>(g.nrec) * sizeof(Rec);
+    if (tc) region_bytes = std::max(region_bytes, tc_region_bytes(n));
+    region_bytes = (region_bytes + 255) & ~static_cast<size_t>(255);
+    Rec *E = reinterpret_cast<Rec *>(region);
+    double *partial = reinterpret_cast<double *>(region + region_bytes);
     const int prep_threads = 256;
     const int64_t prep_blocks_full = (g.nrec + prep_threads - 1) / prep_threads;
     const int prep_blocks = static_cast<int>(std::min<int64_t>(prep_blocks_full, sm_count() * 8));
@@ -793,11 +816,16 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
         k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                  static_cast<const int32_t *>(p->y),
                                                  static_cast<const int32_t *>(p->z), n, r2, hdr,
-                                                 d_count);
+                                                 d_count, tc ? 1 : 0);
         CC_CUDA(cudaGetLastError());
         k_fill_i32<<<prep_blocks, prep_threads, 0, stream>>>(
             static_cast<const int32_t *>(p->x), static_cast<const int32_t *>(p->y),
             static_cast<const int32_t *>(p->z), n, g.nrec, E, hdr);
+        CC_CUDA(cudaGetLastError());
+        if (tc) {
+            st = tc_enqueue_fill(p, n, region, hdr, stream);
+            if (st != CC_OK) return st;
+        }
     } else {
         k_fill_f32<<<prep_blocks, prep_threads, 0, stream>>>(
             static_cast<const float *>(p->x), static_cast<const float *>(p->y),
@@ -821,6 +849,12 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool prof = profiling();
     if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
+    // In tensor-core mode the device picks between the two kernels: each returns at once
+    // unless the preparation kernel chose its mode.
+    if (tc) {
+        st = tc_enqueue_pairs(n, region, hdr, d_count, stream);
+        if (st != CC_OK) return st;
+    }
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.threads), args, L.smem, stream));
     if (prof) profile_end(stream, e0, e1);
     return CC_OK;
@@ -850,7 +884,7 @@ cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned 
         const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
         k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                  static_cast<const int32_t *>(p->y),
-                                                 static_cast<const int32_t *>(p->z), n, r2, hdr, d_count);
+                                                 static_cast<const int32_t *>(p->z), n, r2, hdr, d_count, 0);
         k_fill_i32<<<blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                static_cast<const int32_t *>(p->y),
                                                static_cast<const int32_t *>(p->z), n, nrec, E, hdr);
@@ -894,7 +928,7 @@ cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t
     const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
     k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                              static_cast<const int32_t *>(p->y),
-                                             static_cast<const int32_t *>(p->z), n, 0u, hdr, nullptr);
+                                             static_cast<const int32_t *>(p->z), n, 0u, hdr, nullptr, 0);
     CC_CUDA(cudaGetLastError());
     return CC_OK;
 }

@@ -1,0 +1,442 @@
+// Tensor-core pair kernel for integer points (fast exact mode): the balanced cyclic
+// schedule of Section 4 with the per-pair collision predicate evaluated as a dense
+// contraction on the 5th-generation tensor cores (tcgen05, kind::tf32, FP32 accumulation
+// in Tensor Memory).
+//
+// With centred integer coordinates p' (|p'| <= m per axis) and n = |p'|^2,
+//     d^2 - r2e - 1 = -2 p'_i . p'_j + n_j + (n_i - r2e - 1) = sum_k a_ik * b_jk
+// over K = 8 slots:
+//     a_i = [-2x'_i, -2y'_i, -2z'_i, 1, 1, cA*2^22, cB*2^11, cC]
+//     b_j = [ x'_j,   y'_j,   z'_j, nH*2^11, nL, 1, 1, 1]
+// where n_j = nH*2^11 + nL (0 <= nL < 2^11) and c_i = n_i - r2e - 1 = cA*2^22 + cB*2^11 + cC
+// with balanced digits cB, cC in [-1024, 1023]. Every operand is an integer of at most
+// 11 significant bits times a power of two, so it is exact in TF32, every product is
+// exact, and the mode test on the device admits the TF32 path only when the sum of the
+// absolute values of all eight terms stays below 2^24. Then every partial sum, in any
+// order and with any alignment the tensor core uses, is an integer below 2^24 and exact
+// in FP32: the accumulator holds d^2 - r2e - 1 exactly, and the pair collides (d^2 <= r2)
+// iff it is negative.
+//
+// Counting the negatives: with acc in [2^23, 2^24) (unit spacing), fma.rm(v, 2^-25, acc)
+// gives acc - 1 if v <= -1 and acc if v >= 0 (|v| < 2^24 keeps |v| 2^-25 below 1/2), so
+// one packed FP32x2 instruction counts two pairs exactly.
+//
+// Per CTA (one per SM, persistent, an equal contiguous share of the (tile, stage) units):
+//   warp 0        bulk-copies the i-tile operand (128 rows, 4 KB) when the tile changes
+//                 and every j-stage operand (256 rows, 8 KB) into an NS-deep ring,
+//   warp 1        allocates 512 TMEM columns; its lane 0 issues one
+//                 tcgen05.mma (M=128, N=256, K=8) per unit into one of two TMEM
+//                 accumulators and commits to the ring / accumulator barriers,
+//   warps 2..     (EPW warps) read the accumulator rows of their TMEM lane quarter
+//                 (tcgen05.ld 32x32b) and count; stages that touch the ends of the
+//                 cyclic range take the per-pair validity mask.
+// Every wait is bounded by the global timer; on expiry the kernel records ST_TIMEOUT,
+// lets the other roles stop, waits (bounded) for its MMAs, frees TMEM and returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "cc_internal.cuh"
+#include "cc_tcgen05.cuh"
+
+namespace cc {
+
+constexpr int TC_T = 128;          // objects per i-tile (MMA M)
+constexpr int TC_JS = 256;         // objects per j-stage (MMA N)
+constexpr int TC_ROW = 32;         // bytes per operand row (8 TF32)
+constexpr int TC_ATILE = TC_T * TC_ROW;    // 4096
+constexpr int TC_BSTAGE = TC_JS * TC_ROW;  // 8192
+
+// Byte offset of element k of row r in the no-swizzle K-major core-matrix layout:
+// 8-row groups of 256 bytes, each two 128-byte core matrices (k 0-3, k 4-7).
+__host__ __device__ constexpr uint32_t tc_off(int64_t r, int k) {
+    return static_cast<uint32_t>((r & 7) * 16 + (k >> 2) * 128 + (k & 3) * 4);
+}
+__host__ __device__ constexpr int64_t tc_group(int64_t r) { return (r >> 3) * 256; }
+
+struct TcGeom {
+    int64_t M, K, units, elen;
+    size_t a_bytes, b_bytes;
+};
+
+TcGeom tc_geometry(int64_t n) {
+    TcGeom g;
+    const int64_t h = (n - 1) / 2;
+    g.M = (n + TC_T - 1) / TC_T;
+    g.K = (TC_T + h + 1 + TC_JS - 1) / TC_JS;
+    g.units = g.M * g.K;
+    g.elen = (g.M - 1) * TC_T + g.K * TC_JS;
+    g.a_bytes = static_cast<size_t>(g.M) * TC_ATILE;
+    g.b_bytes = static_cast<size_t>(g.elen) * TC_ROW;
+    return g;
+}
+
+size_t tc_region_bytes(int64_t n) {
+    const TcGeom g = tc_geometry(n);
+    return g.a_bytes + g.b_bytes;
+}
+
+// ---------------------------------------------------------------------------------------
+// operand fill (runs only when the device chose MODE_I32_TC)
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_fill_tc(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
+                          const int32_t *__restrict__ z, int64_t n, int64_t arows, int64_t elen,
+                          uint8_t *__restrict__ Aop, uint8_t *__restrict__ Bop, const WsHeader *__restrict__ h) {
+    if (h->mode != MODE_I32_TC) return;
+    const int32_t cx = h->cx, cy = h->cy, cz = h->cz;
+    const int32_t off = h->ai_off;   // r2e + 1
+    const int64_t rows = arows > elen ? arows : elen;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t *ga = Aop + tc_group(r);
+        uint8_t *gb = Bop + tc_group(r);
+        if (r < arows) {
+            float4 lo, hi;
+            if (r < n) {
+                const int32_t xi = x[r] - cx, yi = y[r] - cy, zi = z[r] - cz;
+                const int32_t c = xi * xi + yi * yi + zi * zi - off;
+                const int32_t cC = ((c + 1024) & 2047) - 1024;
+                const int32_t c1 = (c - cC) >> 11;   // exact: c - cC is a multiple of 2^11
+                const int32_t cB = ((c1 + 1024) & 2047) - 1024;
+                const int32_t cA = (c1 - cB) >> 11;
+                lo = make_float4(static_cast<float>(-2 * xi), static_cast<float>(-2 * yi),
+                                 static_cast<float>(-2 * zi), 1.0f);
+                hi = make_float4(1.0f, static_cast<float>(cA) * 4194304.0f, static_cast<float>(cB) * 2048.0f,
+                                 static_cast<float>(cC));
+            } else {
+                // ragged tile end: v = 1 for every j, never a hit
+                lo = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                hi = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+            }
+            *reinterpret_cast<float4 *>(ga + tc_off(r, 0)) = lo;
+            *reinterpret_cast<float4 *>(ga + tc_off(r, 4)) = hi;
+        }
+        if (r < elen) {
+            const int64_t p = r < n ? r : r % n;
+            const int32_t xj = x[p] - cx, yj = y[p] - cy, zj = z[p] - cz;
+            const int32_t nj = xj * xj + yj * yj + zj * zj;
+            const float4 lo = make_float4(static_cast<float>(xj), static_cast<float>(yj),
+                                          static_cast<float>(zj), static_cast<float>(nj >> 11) * 2048.0f);
+            const float4 hi = make_float4(static_cast<float>(nj & 2047), 1.0f, 1.0f, 1.0f);
+            *reinterpret_cast<float4 *>(gb + tc_off(r, 0)) = lo;
+            *reinterpret_cast<float4 *>(gb + tc_off(r, 4)) = hi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------------------
+
+struct TcArgs {
+    const uint8_t *Aop;     // i-tile operands, M tiles of 4 KB
+    const uint8_t *Bop;     // extended j operands, elen rows
+    int64_t n;
+    int64_t units;          // M * K
+    int32_t K;              // stages per tile
+    int32_t h;              // (n-1)/2
+    WsHeader *hdr;
+    unsigned long long *d_count;
+    uint64_t wait_ns;
+    int32_t stall;          // test hook: the copy warp issues nothing
+    int32_t pad;
+};
+
+template <int EPW, int NS>
+struct TcSmem {
+    static constexpr int kA = 0;                          // 2 i-tile slots
+    static constexpr int kB = 2 * TC_ATILE;               // NS j-stage slots
+    static constexpr int kBars = kB + NS * TC_BSTAGE;
+    // a_full[2] a_empty[2] b_full[NS] b_empty[NS] t_full[2] t_empty[2] done
+    static constexpr int kNBars = 9 + 2 * NS;
+    static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag
+    static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
+    static constexpr int kTotal = kRed + EPW * 8;
+};
+
+__device__ __forceinline__ f2 f2_fma_rm(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// acc lanes start at 2^24 - 1 (0x4B7FFFFF); the count is 2^24 - 1 - acc = ~bits & 0x7FFFFF.
+constexpr f2 kAccInit = 0x4B7FFFFF4B7FFFFFull;
+constexpr f2 kScale = 0x3300000033000000ull;   // 2^-25 in both lanes
+
+__device__ __forceinline__ uint32_t acc_count(f2 a) {
+    const uint32_t lo = static_cast<uint32_t>(a), hi = static_cast<uint32_t>(a >> 32);
+    return ((~lo) & 0x7FFFFFu) + ((~hi) & 0x7FFFFFu);
+}
+
+template <int EPW, int NS>
+__global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
+    using L = TcSmem<EPW, NS>;
+    static_assert(EPW % 4 == 0, "epilogue warps cover the four TMEM lane quarters equally");
+    constexpr int CPW = TC_JS / (EPW / 4);   // accumulator columns per epilogue warp
+    static_assert(CPW == 128, "one x128 TMEM load per epilogue warp and unit");
+    extern __shared__ __align__(1024) uint8_t smem[];
+    if (A.hdr->mode != MODE_I32_TC) return;   // uniform: another kernel handles this call
+
+    uint8_t *sA = smem + L::kA;
+    uint8_t *sB = smem + L::kB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
+    uint64_t *a_full = bars, *a_empty = bars + 2;
+    uint64_t *b_full = bars + 4, *b_empty = bars + 4 + NS;
+    uint64_t *t_full = bars + 4 + 2 * NS, *t_empty = t_full + 2, *done = t_full + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], EPW);
+        }
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&b_full[i], 1);
+            mbar_init(&b_empty[i], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    const int64_t G = gridDim.x;
+    const int64_t u0 = (A.units * blockIdx.x) / G;
+    const int64_t u1 = (A.units * (blockIdx.x + 1)) / G;
+    const int64_t K = A.K;
+    if (warp == 0) {
+        // ------------------------------- copy warp -------------------------------------
+        if (lane == 0 && !A.stall) {
+            int64_t t = u0 / K, s = u0 - (u0 / K) * K;   // unit u = t*K + s
+            int64_t cur_t = -1;
+            uint32_t na = 0;
+            int64_t q = 0;
+            for (int64_t u = u0; u < u1; ++u, ++q) {
+                if (t != cur_t) {
+                    const uint32_t as = na & 1u;
+                    if (!mbar_wait_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
+                    mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
+                    bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
+                    ++na;
+                    cur_t = t;
+                }
+                const int slot = static_cast<int>(q % NS);
+                if (!mbar_wait_bounded(&b_empty[slot], static_cast<uint32_t>(((q / NS) & 1) ^ 1), A.wait_ns,
+                                       abort_flag))
+                    break;
+                mbar_arrive_expect_tx(&b_full[slot], TC_BSTAGE);
+                bulk_g2s(sB + slot * TC_BSTAGE, A.Bop + (t * TC_T + s * TC_JS) * TC_ROW, TC_BSTAGE, &b_full[slot]);
+                if (++s == K) {
+                    s = 0;
+                    ++t;
+                }
+            }
+            // Every copy issued above is waited for by the MMA lane before it retires the
+            // slot; after an abort the MMA lane may have stopped early, so wait here
+            // (bounded) for the last copy of every slot and of both i-tile slots.
+            if (*abort_flag) {
+                const int64_t issued = q;
+                for (int64_t qq = issued > NS ? issued - NS : 0; qq < issued; ++qq)
+                    (void)mbar_wait_bounded(&b_full[qq % NS], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
+                for (uint32_t k = (na > 2 ? na - 2 : 0); k < na; ++k)
+                    (void)mbar_wait_bounded(&a_full[k & 1u], (k >> 1) & 1u, A.wait_ns);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------- MMA lane --------------------------------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32_f32(TC_T, TC_JS);
+            int64_t s = u0 - (u0 / K) * K;
+            bool new_tile = true;
+            uint32_t na = 0;
+            int64_t q = 0;
+            bool ok = true;
+            for (int64_t u = u0; u < u1; ++u, ++q) {
+                if (new_tile) {
+                    ok = mbar_spin_bounded(&a_full[na & 1u], (na >> 1) & 1u, A.wait_ns, abort_flag);
+                    if (!ok) break;
+                    ++na;
+                }
+                const uint32_t as = (na - 1) & 1u;
+                const int slot = static_cast<int>(q % NS);
+                const int buf = static_cast<int>(q & 1);
+                ok = mbar_spin_bounded(&b_full[slot], static_cast<uint32_t>((q / NS) & 1), A.wait_ns, abort_flag) &&
+                     mbar_spin_bounded(&t_empty[buf], static_cast<uint32_t>(((q >> 1) & 1) ^ 1), A.wait_ns,
+                                       abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t ad = smem_desc_k_noswizzle(smem_u32(sA + as * TC_ATILE), 128, 256);
+                const uint64_t bd = smem_desc_k_noswizzle(smem_u32(sB + slot * TC_BSTAGE), 128, 256);
+                tc_mma_tf32(tbase + static_cast<uint32_t>(buf * TC_JS), ad, bd, idesc, 0u);
+                tc_commit(&b_empty[slot]);
+                tc_commit(&t_full[buf]);
+                new_tile = ++s == K;
+                if (new_tile) s = 0;
+                if (new_tile || u + 1 == u1) tc_commit(&a_empty[as]);
+            }
+            if (!ok) {
+                atomicOr(&A.hdr->status, ST_TIMEOUT);
+                *abort_flag = 1;
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            tc_commit(done);
+            if (!mbar_wait_bounded(done, 0u, A.wait_ns)) atomicOr(&A.hdr->status, ST_TIMEOUT);
+        }
+    } else {
+        // ------------------------------- epilogue warps --------------------------------
+        const int ew = warp - 2;
+        const int quarter = warp & 3;          // TMEM lanes this warp may access
+        const int part = ew >> 2;              // which CPW-column part of the accumulator
+        const int row = quarter * 32 + lane;   // object offset inside the i-tile
+        const uint32_t lane_addr = static_cast<uint32_t>(quarter * 32) << 16;
+        f2 acc[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
+        unsigned long long cnt = 0;
+        int64_t t = u0 / K, s = u0 - (u0 / K) * K;
+        int64_t q = 0;
+        for (int64_t u = u0; u < u1; ++u, ++q) {
+            const int32_t eo0 = static_cast<int32_t>(s) * TC_JS;
+            const int buf = static_cast<int>(q & 1);
+            // warp-uniform outcome: the TMEM loads below are .sync.aligned
+            const bool got =
+                __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], static_cast<uint32_t>((q >> 1) & 1),
+                                                          A.wait_ns, abort_flag));
+            if (!got) {
+                if (lane == 0) {
+                    atomicOr(&A.hdr->status, ST_TIMEOUT);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            uint32_t v[CPW];
+            tmem_ld128(tbase + lane_addr + static_cast<uint32_t>(buf * TC_JS + part * CPW), v);
+            // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
+            // before counting, so the next MMA overlaps this warp's arithmetic
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[buf]);
+            const bool full = eo0 >= TC_T && eo0 + TC_JS - 1 <= A.h;
+            if (full) {
+#pragma unroll
+                for (int j = 0; j < CPW / 2; ++j) {
+                    const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
+                    acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
+                }
+            } else {
+                const int64_t i = t * TC_T + row;
+                const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
+                const int64_t d0 = static_cast<int64_t>(eo0) + part * CPW - row;   // e - i of column 0
+#pragma unroll
+                for (int j = 0; j < CPW; ++j)
+                    cnt += (d0 + j >= 1 && d0 + j <= ev && __uint_as_float(v[j]) < 0.0f) ? 1u : 0u;
+            }
+            if ((q & 1023) == 1023) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    cnt += acc_count(acc[a]);
+                    acc[a] = kAccInit;
+                }
+            }
+            if (++s == K) {
+                s = 0;
+                ++t;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) cnt += acc_count(acc[a]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+        if (lane == 0) red[ew] = cnt;
+    }
+    __syncwarp();   // lanes 1-31 of the copy and MMA warps wait for their lane 0
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long c = 0;
+        for (int i = 0; i < EPW; ++i) c += red[i];
+        if (c && A.d_count) atomicAdd(A.d_count, c);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+
+constexpr int TC_EPW = 8;
+constexpr int TC_NS = 12;
+// Dynamic shared memory requested per CTA: more than half of the SM's 228 KB, so that
+// exactly one CTA (and one 512-column TMEM allocation) is resident per SM.
+constexpr int TC_SMEM_REQ = 120 * 1024;
+
+bool tc_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("CC_TC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Enqueues the operand fill and the tensor-core kernel; both do nothing unless the
+// preparation kernel chose MODE_I32_TC for this call. `region` holds tc_region_bytes(n).
+cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream) {
+    const TcGeom g = tc_geometry(n);
+    const int64_t rows = std::max<int64_t>(g.M * TC_T, g.elen);
+    const int blocks = static_cast<int>(std::min<int64_t>((rows + 255) / 256, static_cast<int64_t>(sm_count()) * 8));
+    k_fill_tc<<<blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x), static_cast<const int32_t *>(p->y),
+                                          static_cast<const int32_t *>(p->z), n, g.M * TC_T, g.elen, region,
+                                          region + g.a_bytes, hdr);
+    CC_CUDA(cudaGetLastError());
+    return CC_OK;
+}
+
+cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
+                           cudaStream_t stream) {
+    using L = TcSmem<TC_EPW, TC_NS>;
+    static_assert(L::kTotal <= TC_SMEM_REQ, "shared memory layout");
+    auto fn = k_pairs_tc<TC_EPW, TC_NS>;
+    static bool attr = false;
+    if (!attr) {
+        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
+        attr = true;
+    }
+    const TcGeom g = tc_geometry(n);
+    TcArgs A;
+    A.Aop = region;
+    A.Bop = region + g.a_bytes;
+    A.n = n;
+    A.units = g.units;
+    A.K = static_cast<int32_t>(g.K);
+    A.h = static_cast<int32_t>((n - 1) / 2);
+    A.hdr = hdr;
+    A.d_count = d_count;
+    A.wait_ns = wait_limit_ns();
+    A.stall = debug_stall();
+    A.pad = 0;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g.units, sm_count())));
+    void *args[] = {&A};
+    CC_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(fn), dim3(grid), dim3((2 + TC_EPW) * 32), args,
+                             TC_SMEM_REQ, stream));
+    return CC_OK;
+}
+
+}  // namespace cc
