@@ -42,11 +42,9 @@
 
 namespace cc {
 
-constexpr int TC_T = 128;          // objects per i-tile (MMA M)
-constexpr int TC_JS = 256;         // objects per j-stage (MMA N)
-constexpr int TC_ROW = 32;         // bytes per operand row (8 TF32)
+constexpr int TC_T = 128;                  // objects per i-tile (MMA M)
+constexpr int TC_ROW = 32;                 // bytes per operand row (8 TF32)
 constexpr int TC_ATILE = TC_T * TC_ROW;    // 4096
-constexpr int TC_BSTAGE = TC_JS * TC_ROW;  // 8192
 
 // Byte offset of element k of row r in the no-swizzle K-major core-matrix layout:
 // 8-row groups of 256 bytes, each two 128-byte core matrices (k 0-3, k 4-7).
@@ -55,26 +53,32 @@ __host__ __device__ constexpr uint32_t tc_off(int64_t r, int k) {
 }
 __host__ __device__ constexpr int64_t tc_group(int64_t r) { return (r >> 3) * 256; }
 
+// Geometry of one call for j-stages of JS objects (the MMA's N).
 struct TcGeom {
     int64_t M, K, units, elen;
     size_t a_bytes, b_bytes;
 };
 
-TcGeom tc_geometry(int64_t n) {
+TcGeom tc_geometry(int64_t n, int js) {
     TcGeom g;
     const int64_t h = (n - 1) / 2;
     g.M = (n + TC_T - 1) / TC_T;
-    g.K = (TC_T + h + 1 + TC_JS - 1) / TC_JS;
+    g.K = (TC_T + h + 1 + js - 1) / js;
     g.units = g.M * g.K;
-    g.elen = (g.M - 1) * TC_T + g.K * TC_JS;
+    g.elen = (g.M - 1) * TC_T + g.K * js;
     g.a_bytes = static_cast<size_t>(g.M) * TC_ATILE;
     g.b_bytes = static_cast<size_t>(g.elen) * TC_ROW;
     return g;
 }
 
+// Operand bytes for any of the compiled stage widths (128 or 256).
 size_t tc_region_bytes(int64_t n) {
-    const TcGeom g = tc_geometry(n);
-    return g.a_bytes + g.b_bytes;
+    size_t b = 0;
+    for (int js : {128, 256}) {
+        const TcGeom g = tc_geometry(n, js);
+        b = std::max(b, g.a_bytes + g.b_bytes);
+    }
+    return b;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -144,13 +148,14 @@ struct TcArgs {
     int32_t pad;
 };
 
-template <int EPW, int NS>
+template <int JS, int NB, int EPW, int NS>
 struct TcSmem {
+    static constexpr int kStage = JS * TC_ROW;            // bytes of one j-stage
     static constexpr int kA = 0;                          // 2 i-tile slots
     static constexpr int kB = 2 * TC_ATILE;               // NS j-stage slots
-    static constexpr int kBars = kB + NS * TC_BSTAGE;
-    // a_full[2] a_empty[2] b_full[NS] b_empty[NS] t_full[2] t_empty[2] done
-    static constexpr int kNBars = 9 + 2 * NS;
+    static constexpr int kBars = kB + NS * kStage;
+    // a_full[2] a_empty[2] b_full[NS] b_empty[NS] t_full[NB] t_empty[NB] done
+    static constexpr int kNBars = 5 + 2 * NS + 2 * NB;
     static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
     static constexpr int kTotal = kRed + EPW * 8;
@@ -171,12 +176,16 @@ __device__ __forceinline__ uint32_t acc_count(f2 a) {
     return ((~lo) & 0x7FFFFFu) + ((~hi) & 0x7FFFFFu);
 }
 
-template <int EPW, int NS>
+// JS objects per j-stage (MMA N), NB accumulators of JS TMEM columns (NB * JS = 512),
+// EPW epilogue warps, NS-deep j-stage ring.
+template <int JS, int NB, int EPW, int NS>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
-    using L = TcSmem<EPW, NS>;
+    using L = TcSmem<JS, NB, EPW, NS>;
+    static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
     static_assert(EPW % 4 == 0, "epilogue warps cover the four TMEM lane quarters equally");
-    constexpr int CPW = TC_JS / (EPW / 4);   // accumulator columns per epilogue warp
-    static_assert(CPW == 128, "one x128 TMEM load per epilogue warp and unit");
+    constexpr int CPW = JS / (EPW / 4);   // accumulator columns per epilogue warp and unit
+    static_assert(CPW == 32 || CPW == 64 || CPW == 128, "one TMEM load per epilogue warp and unit");
+    constexpr int kStage = L::kStage;
     extern __shared__ __align__(1024) uint8_t smem[];
     if (A.hdr->mode != MODE_I32_TC) return;   // uniform: another kernel handles this call
 
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
     uint64_t *a_full = bars, *a_empty = bars + 2;
     uint64_t *b_full = bars + 4, *b_empty = bars + 4 + NS;
-    uint64_t *t_full = bars + 4 + 2 * NS, *t_empty = t_full + 2, *done = t_full + 4;
+    uint64_t *t_full = bars + 4 + 2 * NS, *t_empty = t_full + NB, *done = t_full + 2 * NB;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
@@ -195,6 +204,8 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < NB; ++i) {
             mbar_init(&t_full[i], 1);
             mbar_init(&t_empty[i], EPW);
         }
@@ -229,18 +240,18 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             for (int64_t u = u0; u < u1; ++u, ++q) {
                 if (t != cur_t) {
                     const uint32_t as = na & 1u;
-                    if (!mbar_wait_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
+                    if (!mbar_spin_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
                     mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
                     bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
                     ++na;
                     cur_t = t;
                 }
                 const int slot = static_cast<int>(q % NS);
-                if (!mbar_wait_bounded(&b_empty[slot], static_cast<uint32_t>(((q / NS) & 1) ^ 1), A.wait_ns,
+                if (!mbar_spin_bounded(&b_empty[slot], static_cast<uint32_t>(((q / NS) & 1) ^ 1), A.wait_ns,
                                        abort_flag))
                     break;
-                mbar_arrive_expect_tx(&b_full[slot], TC_BSTAGE);
-                bulk_g2s(sB + slot * TC_BSTAGE, A.Bop + (t * TC_T + s * TC_JS) * TC_ROW, TC_BSTAGE, &b_full[slot]);
+                mbar_arrive_expect_tx(&b_full[slot], kStage);
+                bulk_g2s(sB + slot * kStage, A.Bop + (t * TC_T + s * JS) * TC_ROW, kStage, &b_full[slot]);
                 if (++s == K) {
                     s = 0;
                     ++t;
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     } else if (warp == 1) {
         // ------------------------------- MMA lane --------------------------------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32_f32(TC_T, TC_JS);
+            constexpr uint32_t idesc = idesc_tf32_f32(TC_T, JS);
             int64_t s = u0 - (u0 / K) * K;
             bool new_tile = true;
             uint32_t na = 0;
@@ -274,15 +285,15 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 }
                 const uint32_t as = (na - 1) & 1u;
                 const int slot = static_cast<int>(q % NS);
-                const int buf = static_cast<int>(q & 1);
+                const int buf = static_cast<int>(q % NB);
                 ok = mbar_spin_bounded(&b_full[slot], static_cast<uint32_t>((q / NS) & 1), A.wait_ns, abort_flag) &&
-                     mbar_spin_bounded(&t_empty[buf], static_cast<uint32_t>(((q >> 1) & 1) ^ 1), A.wait_ns,
+                     mbar_spin_bounded(&t_empty[buf], static_cast<uint32_t>(((q / NB) & 1) ^ 1), A.wait_ns,
                                        abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 const uint64_t ad = smem_desc_k_noswizzle(smem_u32(sA + as * TC_ATILE), 128, 256);
-                const uint64_t bd = smem_desc_k_noswizzle(smem_u32(sB + slot * TC_BSTAGE), 128, 256);
-                tc_mma_tf32(tbase + static_cast<uint32_t>(buf * TC_JS), ad, bd, idesc, 0u);
+                const uint64_t bd = smem_desc_k_noswizzle(smem_u32(sB + slot * kStage), 128, 256);
+                tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad, bd, idesc, 0u);
                 tc_commit(&b_empty[slot]);
                 tc_commit(&t_full[buf]);
                 new_tile = ++s == K;
@@ -309,11 +320,11 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         int64_t t = u0 / K, s = u0 - (u0 / K) * K;
         int64_t q = 0;
         for (int64_t u = u0; u < u1; ++u, ++q) {
-            const int32_t eo0 = static_cast<int32_t>(s) * TC_JS;
-            const int buf = static_cast<int>(q & 1);
+            const int32_t eo0 = static_cast<int32_t>(s) * JS;
+            const int buf = static_cast<int>(q % NB);
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
             const bool got =
-                __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], static_cast<uint32_t>((q >> 1) & 1),
+                __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], static_cast<uint32_t>((q / NB) & 1),
                                                           A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
@@ -324,13 +335,13 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             }
             tc_fence_after();
             uint32_t v[CPW];
-            tmem_ld128(tbase + lane_addr + static_cast<uint32_t>(buf * TC_JS + part * CPW), v);
+            tmem_ld<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
             // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
             // before counting, so the next MMA overlaps this warp's arithmetic
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&t_empty[buf]);
-            const bool full = eo0 >= TC_T && eo0 + TC_JS - 1 <= A.h;
+            const bool full = eo0 >= TC_T && eo0 + JS - 1 <= A.h;
             if (full) {
 #pragma unroll
                 for (int j = 0; j < CPW / 2; ++j) {
@@ -381,8 +392,6 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
 // host side
 // ---------------------------------------------------------------------------------------
 
-constexpr int TC_EPW = 8;
-constexpr int TC_NS = 12;
 // Dynamic shared memory requested per CTA: more than half of the SM's 228 KB, so that
 // exactly one CTA (and one 512-column TMEM allocation) is resident per SM.
 constexpr int TC_SMEM_REQ = 120 * 1024;
@@ -396,10 +405,54 @@ bool tc_enabled() {
     return v == 1;
 }
 
-// Enqueues the operand fill and the tensor-core kernel; both do nothing unless the
-// preparation kernel chose MODE_I32_TC for this call. `region` holds tc_region_bytes(n).
+struct TcLaunch {
+    const void *fn;
+    int js, threads;
+};
+
+template <int JS, int NB, int EPW, int NS>
+static cc_status tc_launch_of(TcLaunch &L) {
+    static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
+    auto fn = k_pairs_tc<JS, NB, EPW, NS>;
+    static bool attr = false;
+    if (!attr) {
+        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
+        attr = true;
+    }
+    L.fn = reinterpret_cast<const void *>(fn);
+    L.js = JS;
+    L.threads = (2 + EPW) * 32;
+    return CC_OK;
+}
+
+// Compiled shapes (CC_TC_VARIANT selects one for sweeps; the default is the measured best).
+static int tc_variant() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("CC_TC_VARIANT");
+        v = e ? atoi(e) : 0;
+        if (v < 0 || v > 4) v = 0;
+    }
+    return v;
+}
+
+static cc_status tc_pick(TcLaunch &L) {
+    switch (tc_variant()) {
+        case 1: return tc_launch_of<128, 4, 8, 16>(L);
+        case 2: return tc_launch_of<128, 4, 4, 16>(L);
+        case 3: return tc_launch_of<256, 2, 16, 12>(L);
+        case 4: return tc_launch_of<128, 4, 16, 16>(L);
+        default: return tc_launch_of<256, 2, 8, 12>(L);
+    }
+}
+
+// Enqueues the operand fill; it does nothing unless the preparation kernel chose
+// MODE_I32_TC for this call. `region` holds tc_region_bytes(n).
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream) {
-    const TcGeom g = tc_geometry(n);
+    TcLaunch L;
+    cc_status st = tc_pick(L);
+    if (st != CC_OK) return st;
+    const TcGeom g = tc_geometry(n, L.js);
     const int64_t rows = std::max<int64_t>(g.M * TC_T, g.elen);
     const int blocks = static_cast<int>(std::min<int64_t>((rows + 255) / 256, static_cast<int64_t>(sm_count()) * 8));
     k_fill_tc<<<blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x), static_cast<const int32_t *>(p->y),
@@ -409,17 +462,13 @@ cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHead
     return CC_OK;
 }
 
+// Enqueues the tensor-core kernel (returns at once unless the mode is MODE_I32_TC).
 cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
                            cudaStream_t stream) {
-    using L = TcSmem<TC_EPW, TC_NS>;
-    static_assert(L::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<TC_EPW, TC_NS>;
-    static bool attr = false;
-    if (!attr) {
-        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
-        attr = true;
-    }
-    const TcGeom g = tc_geometry(n);
+    TcLaunch L;
+    cc_status st = tc_pick(L);
+    if (st != CC_OK) return st;
+    const TcGeom g = tc_geometry(n, L.js);
     TcArgs A;
     A.Aop = region;
     A.Bop = region + g.a_bytes;
@@ -434,8 +483,7 @@ cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsi
     A.pad = 0;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g.units, sm_count())));
     void *args[] = {&A};
-    CC_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(fn), dim3(grid), dim3((2 + TC_EPW) * 32), args,
-                             TC_SMEM_REQ, stream));
+    CC_CUDA(cudaLaunchKernel(L.fn, dim3(grid), dim3(L.threads), args, TC_SMEM_REQ, stream));
     return CC_OK;
 }
 

@@ -4,7 +4,7 @@
 //   * shared-memory matrix descriptors for K-major operands without swizzling,
 //   * the instruction descriptor of kind::tf32 with FP32 accumulation,
 //   * tcgen05.mma issue, tcgen05.commit to an mbarrier, the thread-sync fences,
-//   * tcgen05.ld of 32 columns (32x32b shape) fused with its wait.
+//   * tcgen05.ld of 32, 64 or 128 columns (32x32b shape) fused with its wait.
 #pragma once
 
 #include <stdint.h>
@@ -93,6 +93,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "memory");
 }
 
+// Same for 64 consecutive columns.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {"
+        "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63"
+        "}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        :
+          "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+          "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+          "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr)
+        : "memory");
+}
+
 // Same for 128 consecutive columns (one x128 load, one wait).
 __device__ __forceinline__ void tmem_ld128(uint32_t taddr, uint32_t (&v)[128]) {
     asm volatile(
@@ -126,6 +149,14 @@ __device__ __forceinline__ void tmem_ld128(uint32_t taddr, uint32_t (&v)[128]) {
           "=r"(v[120]), "=r"(v[121]), "=r"(v[122]), "=r"(v[123]), "=r"(v[124]), "=r"(v[125]), "=r"(v[126]), "=r"(v[127])
         : "r"(taddr)
         : "memory");
+}
+
+template <int C>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[C]) {
+    static_assert(C == 32 || C == 64 || C == 128, "column count");
+    if constexpr (C == 32) tmem_ld32(taddr, v);
+    else if constexpr (C == 64) tmem_ld64(taddr, v);
+    else tmem_ld128(taddr, v);
 }
 
 #endif  // __CUDACC__
