@@ -180,28 +180,35 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
-KERNEL_SOURCES = ("paper_1901_11204_gb300/csrc/cc_single.cu", "paper_1901_11204_gb300/csrc/cc_pairs.cuh",
-                  "paper_1901_11204_gb300/csrc/cc_internal.cuh")
+# Sources of each pair kernel; a committed ncu traffic record is used only while the
+# hash of these files matches the one recorded with it.
+KERNEL_SOURCES = {
+    "fp32": ("paper_1901_11204_gb300/csrc/cc_single.cu", "paper_1901_11204_gb300/csrc/cc_pairs.cuh",
+             "paper_1901_11204_gb300/csrc/cc_internal.cuh"),
+    "tensor": ("paper_1901_11204_gb300/csrc/cc_tc.cu", "paper_1901_11204_gb300/csrc/cc_tcgen05.cuh",
+               "paper_1901_11204_gb300/csrc/cc_internal.cuh"),
+}
+TRAFFIC_FILES = {"fp32": "k_pairs_traffic.json", "tensor": "k_pairs_tc_traffic.json"}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kind: str = "fp32") -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[kind]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def measured_traffic():
+def measured_traffic(kind: str = "fp32"):
     """DRAM bytes per launch of the pair kernel from the committed ncu capture, or None
     when the kernel sources changed since that capture."""
-    p = os.path.join(ROOT, "profiles", "k_pairs_traffic.json")
+    p = os.path.join(ROOT, "profiles", TRAFFIC_FILES[kind])
     if not os.path.exists(p):
         return None, "no capture"
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_sha256") != kernel_source_hash():
+    if d.get("source_sha256") != kernel_source_hash(kind):
         return None, "kernel changed since the capture"
     return float(d["dram_bytes_per_launch"]), d.get("workload", "")
 
@@ -220,6 +227,12 @@ def roofline_peak_int(sms: int, mhz: float) -> float:
     clock per SM and the expanded form needs 4 FP32-pipe operations per pair (three
     products as fused multiply-adds and one add of the per-object constant)."""
     return sms * 128.0 * mhz * 1e6 / 4.0
+
+
+# Tensor-core form: one TF32 contraction of K = 8 terms per pair test (16 flops).
+TC_FLOPS_PER_PAIR = 16
+# TF32 / BF16 dense tensor throughput ratio of the part's nominal figures (1.1 / 2.25 PF).
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def roofline_peak_f32(sms: int, mhz: float) -> float:
@@ -275,6 +288,11 @@ def main():
         step()
     torch.cuda.synchronize()
     want = [cc.as_u64(o) for o in outs]
+    modes = []
+    for (x, y, z, r2), o in zip(dsets, outs):     # which pair kernel the device picks per set
+        cc.count_pairs(x, y, z, r2=r2, out=o)
+        modes.append(cc.stream_mode())
+    tensor = all(m == cc.MODE_TENSOR for m in modes)
 
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -313,19 +331,38 @@ def main():
     # ---- roofline of the dominant kernel (pair kernel) ---------------------------------
     peaks, peak_src = load_peaks()
     fmax = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = roofline_peak_int(sms, fmax) / 1e9
-    achieved = tests_per_step * args.steps / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
-    traffic, traffic_note = measured_traffic()
-    roofline = {
-        "bound": "alu", "kernel": "k_pairs_w (single-set pair kernel)",
-        "achieved": achieved, "peak": peak, "unit": METRIC,
-        "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-        "traffic_note": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch: {traffic_note}",
-        "peak_basis": (f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src} sm_max_mhz) / "
-                       "4 FP32-pipe ops per pair"),
-        "kernel_share_of_step": (kern_ms / dev_ms) if dev_ms > 0 else None,
-        "kernel_launches": kern_launches,
-    }
+    pair_rate = tests_per_step * args.steps / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+    if tensor:
+        traffic, traffic_note = measured_traffic("tensor")
+        peak = float(peaks.get("bf16_tflops", 1900.0)) * TF32_PER_BF16
+        achieved = pair_rate * TC_FLOPS_PER_PAIR / 1e3 if pair_rate else None
+        roofline = {
+            "bound": "tensor", "kernel": "k_pairs_tc (tcgen05 kind::tf32 pair kernel)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_note": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch: {traffic_note}",
+            "peak_basis": (f"{peak_src} bf16_tflops {peaks.get('bf16_tflops')} x {TF32_PER_BF16:.3f} "
+                           "(nominal TF32/BF16 dense ratio); 16 TF32 flops per pair test"),
+            "pair_tests_per_s": pair_rate,
+            "kernel_share_of_step": (kern_ms / dev_ms) if dev_ms > 0 else None,
+            "kernel_launches": kern_launches,
+            "timing_note": "events bracket the tensor-core launch and the FP32-pipe launch that "
+                           "returns at once in tensor mode",
+        }
+    else:
+        traffic, traffic_note = measured_traffic("fp32")
+        peak = roofline_peak_int(sms, fmax) / 1e9
+        achieved = pair_rate
+        roofline = {
+            "bound": "alu", "kernel": "k_pairs_w (FP32-pipe pair kernel)",
+            "achieved": achieved, "peak": peak, "unit": METRIC,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_note": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch: {traffic_note}",
+            "peak_basis": (f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src} sm_max_mhz) / "
+                           "4 FP32-pipe ops per pair"),
+            "kernel_share_of_step": (kern_ms / dev_ms) if dev_ms > 0 else None,
+            "kernel_launches": kern_launches,
+        }
     if achieved and clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / fmax)
 
@@ -367,19 +404,27 @@ def main():
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "input_dtype": "int32 (exact: FP32 arithmetic on integers < 2^24)",
+        "dtype": "tf32" if tensor else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD,
+                   "input_dtype": ("int32 (exact: TF32 products of integers with <= 11 significant bits, "
+                                   "FP32 sums below 2^24)" if tensor else
+                                   "int32 (exact: FP32 arithmetic on integers < 2^24)"),
                    "pair_tests_per_step": tests_per_step, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent sets per GPU)"},
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": 4 * len(sets) * args.steps,
+        # per count: reset, min/max + mode, record fill, operand fill, tensor-core kernel and
+        # FP32-pipe kernel (the kernel and fill of the mode not chosen return at once)
+        "gpu_launches": (6 if tensor else 4) * len(sets) * args.steps,
+        "pair_kernel_modes": modes,
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "counts": got,
     }
 
     if rank == 0 and not args.no_extras:
+        line["fp32_pipe_step"] = bench_fp32_pipe_step(cc, torch, step, outs, want, tests_per_step,
+                                                      roofline_peak_int(sms, fmax) / 1e9, flush)
         line["f32_spheres"] = bench_f32(cc, torch, dev, sms, fmax, peak_src)
         line["batched"] = bench_batched(cc, torch, dev)
         line["serving"] = bench_serving(cc, torch, dev, args.serving_queries)
@@ -393,6 +438,38 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_fp32_pipe_step(cc, torch, step, outs, want, tests_per_step, peak, flush, reps=5):
+    """The same step with the tensor-core kernel switched off (every count on the FP32
+    pipe): what the tensor-core formulation gains on this workload."""
+    cc.set_tensor_cores(False)
+    try:
+        step()
+        torch.cuda.synchronize()
+        mode = cc.stream_mode()
+        stream = torch.cuda.current_stream()
+        cc.profile_enable(True)
+        cc.profile_read()
+        tot = 0.0
+        for k in range(reps):
+            flush.fill_(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        kern_ms, _ = cc.profile_read()
+        cc.profile_enable(False)
+        assert [cc.as_u64(o) for o in outs] == want
+    finally:
+        cc.set_tensor_cores(True)
+    value = tests_per_step * reps / (tot * 1e-3) / 1e9
+    kern = tests_per_step * reps / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+    return {"value": value, "unit": METRIC, "ms_per_step": tot / reps, "mode": mode,
+            "kernel": "k_pairs_w", "kernel_rate": kern, "kernel_frac_of_fp32_pipe_bound": (kern / peak) if kern else None,
+            "counts_equal": True}
 
 
 def _time(fn, reps, torch, stream=None):

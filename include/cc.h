@@ -144,6 +144,13 @@ enum {
 };
 cc_status cc_stream_mode(void *stream, int32_t *mode);
 
+/* Enables (1, the default) or disables (0) the tensor-core kernel for later
+ * cc_count_pairs calls of this process; when disabled every integer count runs on the
+ * FP32 pipe. Results are identical either way (both are exact); the switch exists to
+ * compare the two kernels and to keep the tensor cores free for other work. The initial
+ * value comes from the environment variable CC_TC (0 disables). Always CC_OK. */
+cc_status cc_set_tensor_cores(int32_t enable);
+
 /* Same result as cc_count_pairs, for callers that must not allocate device memory while
  * they run: code recording into a CUDA graph, engines whose single allocator forbids side
  * allocations, services with a fixed memory budget that must not fail mid-run on an

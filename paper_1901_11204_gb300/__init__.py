@@ -71,6 +71,7 @@ _SIGS = {
     "cc_release": ([_VP], ctypes.c_int),
     "cc_stream_status": ([_VP], ctypes.c_int),
     "cc_stream_mode": ([_VP, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cc_set_tensor_cores": ([ctypes.c_int32], ctypes.c_int),
     "cc_plan_create": ([ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
     "cc_plan_destroy": ([_VP], None),
     "cc_count_pairs_batched": ([_VP, _PTS, _VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
@@ -244,6 +245,11 @@ def stream_status(stream=None) -> int:
 # Pair kernel chosen by the device for the last single-set call on a stream
 # (cc_stream_mode): the CC_MODE_* values of cc.h.
 MODE_FP32_EXACT, MODE_INT_WIDE, MODE_RANGE_ERROR, MODE_FP32_SPHERES, MODE_TENSOR = 0, 1, 2, 3, 4
+
+
+def set_tensor_cores(enable: bool) -> None:
+    """Enable (default) or disable the tensor-core pair kernel for later counts."""
+    _check(lib().cc_set_tensor_cores(1 if enable else 0))
 
 
 def stream_mode(stream=None) -> int:

@@ -21,6 +21,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
                          float *d_sum, void *ws, cudaStream_t stream, bool allow_tc);
 cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t stream);
 size_t straight_ws_bytes(int64_t n);
+void tc_set_enabled(bool on);
 size_t linear_ws_bytes(int64_t n);
 cc_status linear_enqueue(const cc_points *p, int64_t n, int contacts, unsigned long long *d_count, void *ws,
                          cudaStream_t s);
@@ -298,6 +299,11 @@ cc_status cc_stream_status(void *stream) {
     CC_CUDA(cudaStreamSynchronize(s));
     if (status & ST_TIMEOUT) return fail(CC_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (status & ST_RANGE) return fail(CC_ERR_RANGE, "integer coordinate span above 32767 on some axis");
+    return CC_OK;
+}
+
+cc_status cc_set_tensor_cores(int32_t enable) {
+    tc_set_enabled(enable != 0);
     return CC_OK;
 }
 

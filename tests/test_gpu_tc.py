@@ -183,3 +183,24 @@ def test_tc_bounded_wait_timeout(cc):
     assert mode == cc.MODE_TENSOR
     assert got == oracle.count_i32(x, y, z, 9)
     assert cc.stream_status() == cc.CC_OK
+
+
+@pytest.mark.parametrize("r2", [9, 400])
+def test_switch_between_kernels_gives_equal_counts(cc, r2):
+    """cc_set_tensor_cores(0) sends the same call to the FP32-pipe kernel: equal counts."""
+    import synth
+    c = synth.cfg2(70001)
+    t = dev(c["x"], c["y"], c["z"])
+    out = cc.count_pairs(*t, r2=r2)
+    torch.cuda.synchronize()
+    assert cc.stream_mode() == cc.MODE_TENSOR
+    a = cc.as_u64(out)
+    cc.set_tensor_cores(False)
+    try:
+        out = cc.count_pairs(*t, r2=r2)
+        torch.cuda.synchronize()
+        assert cc.stream_mode() == cc.MODE_FP32_EXACT
+        b = cc.as_u64(out)
+    finally:
+        cc.set_tensor_cores(True)
+    assert a == b == oracle.count_i32(c["x"], c["y"], c["z"], r2)
