@@ -64,9 +64,9 @@ struct WsHeader {
     uint32_t pad[17];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
-static_assert(MODE_I32_FAST == CC_MODE_FP32_EXACT && MODE_I32_WIDE == CC_MODE_INT_WIDE &&
-                  MODE_RANGE_ERR == CC_MODE_RANGE_ERROR && MODE_F32 == CC_MODE_FP32_SPHERES &&
-                  MODE_I32_TC == CC_MODE_TENSOR,
+static_assert(int{MODE_I32_FAST} == int{CC_MODE_FP32_EXACT} && int{MODE_I32_WIDE} == int{CC_MODE_INT_WIDE} &&
+                  int{MODE_RANGE_ERR} == int{CC_MODE_RANGE_ERROR} && int{MODE_F32} == int{CC_MODE_FP32_SPHERES} &&
+                  int{MODE_I32_TC} == int{CC_MODE_TENSOR},
               "device modes are the public CC_MODE_* values");
 
 // Largest half-span m = ceil(span/2) for which the FP32 expanded-square form is exact:

@@ -159,7 +159,8 @@ struct TcSmem {
     static constexpr int kNBars = 5 + 2 * NS + 2 * NB;
     static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
-    static constexpr int kTotal = kRed + EPW * 8;
+    static constexpr int kSeq = kRed + EPW * 8;           // published unit per accumulator
+    static constexpr int kTotal = kSeq + NB * 8;
 };
 
 __device__ __forceinline__ f2 f2_fma_rm(f2 a, f2 b, f2 c) {
@@ -182,7 +183,10 @@ __device__ __forceinline__ uint32_t acc_count(f2 a) {
 // unit, SCR are screened on the integer ALU (a three-input OR of the raw bits per two
 // values; a set sign bit sends that group to an exact recount, rare unless hits are
 // dense) and the rest counted exactly on the FP32 pipe, so the two pipes share the work.
-template <int JS, int NB, int EPW, int NS, int SCR = 0>
+// LEADER: one epilogue thread polls the accumulator barrier and publishes the unit's
+// sequence number in shared memory; the other epilogue threads poll that word (plain
+// shared loads, no traffic on the barrier unit), and the copy warp waits suspended.
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool LEADER = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -202,6 +206,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
+    volatile long long *seq = reinterpret_cast<volatile long long *>(smem + L::kSeq);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -209,6 +214,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
+        for (int i = 0; i < NB; ++i) seq[i] = 0;
         for (int i = 0; i < NB; ++i) {
             mbar_init(&t_full[i], 1);
             mbar_init(&t_empty[i], EPW);
@@ -234,14 +240,26 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     const int64_t u0 = (A.units * blockIdx.x) / G;
     const int64_t u1 = (A.units * (blockIdx.x + 1)) / G;
     const int64_t K = A.K;
+    // Loop state below is kept in 32-bit counters (ring slot and phase, accumulator and
+    // phase, stage within the tile): the copy and MMA lanes are single threads sharing
+    // their SMSP with two epilogue warps, so their per-unit instruction count is the
+    // pipeline's critical path.
+    const int32_t nu = static_cast<int32_t>(u1 - u0);   // units of this CTA
+    const int32_t K32 = A.K;
+    const int64_t t0 = u0 / K;
+    const int32_t s0 = static_cast<int32_t>(u0 - t0 * K);
     if (warp == 0) {
         // ------------------------------- copy warp -------------------------------------
         if (lane == 0 && !A.stall) {
-            int64_t t = u0 / K, s = u0 - (u0 / K) * K;   // unit u = t*K + s
+            int64_t t = t0;
+            int32_t st = s0;
+            const uint8_t *bsrc = A.Bop + (t * TC_T + static_cast<int64_t>(st) * JS) * TC_ROW;
             int64_t cur_t = -1;
             uint32_t na = 0;
-            int64_t q = 0;
-            for (int64_t u = u0; u < u1; ++u, ++q) {
+            int32_t slot = 0;
+            uint32_t eph = 1;   // parity of the b_empty phase to wait for (first pass: free)
+            int32_t q = 0;
+            for (; q < nu; ++q) {
                 if (t != cur_t) {
                     const uint32_t as = na & 1u;
                     if (!mbar_spin_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
@@ -250,23 +268,28 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     ++na;
                     cur_t = t;
                 }
-                const int slot = static_cast<int>(q % NS);
-                if (!mbar_spin_bounded(&b_empty[slot], static_cast<uint32_t>(((q / NS) & 1) ^ 1), A.wait_ns,
-                                       abort_flag))
-                    break;
+                const bool free_slot = LEADER ? mbar_wait_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)
+                                              : mbar_spin_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag);
+                if (!free_slot) break;
                 mbar_arrive_expect_tx(&b_full[slot], kStage);
-                bulk_g2s(sB + slot * kStage, A.Bop + (t * TC_T + s * JS) * TC_ROW, kStage, &b_full[slot]);
-                if (++s == K) {
-                    s = 0;
+                bulk_g2s(sB + slot * kStage, bsrc, kStage, &b_full[slot]);
+                bsrc += JS * TC_ROW;
+                if (++st == K32) {
+                    st = 0;
                     ++t;
+                    bsrc = A.Bop + t * TC_T * TC_ROW;
+                }
+                if (++slot == NS) {
+                    slot = 0;
+                    eph ^= 1u;
                 }
             }
             // Every copy issued above is waited for by the MMA lane before it retires the
             // slot; after an abort the MMA lane may have stopped early, so wait here
             // (bounded) for the last copy of every slot and of both i-tile slots.
             if (*abort_flag) {
-                const int64_t issued = q;
-                for (int64_t qq = issued > NS ? issued - NS : 0; qq < issued; ++qq)
+                const int32_t issued = q;
+                for (int32_t qq = issued > NS ? issued - NS : 0; qq < issued; ++qq)
                     (void)mbar_wait_bounded(&b_full[qq % NS], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
                 for (uint32_t k = (na > 2 ? na - 2 : 0); k < na; ++k)
                     (void)mbar_wait_bounded(&a_full[k & 1u], (k >> 1) & 1u, A.wait_ns);
@@ -276,33 +299,43 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         // ------------------------------- MMA lane --------------------------------------
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32_f32(TC_T, JS);
-            int64_t s = u0 - (u0 / K) * K;
+            // descriptors of slot 0; a slot's is this plus its byte offset >> 4 (the start
+            // address field cannot carry: shared addresses stay below 2^18)
+            const uint64_t ad0 = smem_desc_k_noswizzle(smem_u32(sA), 128, 256);
+            const uint64_t bd0 = smem_desc_k_noswizzle(smem_u32(sB), 128, 256);
+            int32_t st = s0;
             bool new_tile = true;
             uint32_t na = 0;
-            int64_t q = 0;
+            int32_t slot = 0, buf = 0;
+            uint32_t fph = 0;   // b_full phase parity
+            uint32_t eph = 1;   // t_empty phase parity to wait for (first pass: free)
             bool ok = true;
-            for (int64_t u = u0; u < u1; ++u, ++q) {
+            for (int32_t q = 0; q < nu; ++q) {
                 if (new_tile) {
                     ok = mbar_spin_bounded(&a_full[na & 1u], (na >> 1) & 1u, A.wait_ns, abort_flag);
                     if (!ok) break;
                     ++na;
                 }
                 const uint32_t as = (na - 1) & 1u;
-                const int slot = static_cast<int>(q % NS);
-                const int buf = static_cast<int>(q % NB);
-                ok = mbar_spin_bounded(&b_full[slot], static_cast<uint32_t>((q / NS) & 1), A.wait_ns, abort_flag) &&
-                     mbar_spin_bounded(&t_empty[buf], static_cast<uint32_t>(((q / NB) & 1) ^ 1), A.wait_ns,
-                                       abort_flag);
+                ok = mbar_spin_bounded(&b_full[slot], fph, A.wait_ns, abort_flag) &&
+                     mbar_spin_bounded(&t_empty[buf], eph, A.wait_ns, abort_flag);
                 if (!ok) break;
                 tc_fence_after();
-                const uint64_t ad = smem_desc_k_noswizzle(smem_u32(sA + as * TC_ATILE), 128, 256);
-                const uint64_t bd = smem_desc_k_noswizzle(smem_u32(sB + slot * kStage), 128, 256);
-                tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad, bd, idesc, 0u);
+                tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad0 + as * (TC_ATILE >> 4),
+                            bd0 + static_cast<uint32_t>(slot) * (kStage >> 4), idesc, 0u);
                 tc_commit(&b_empty[slot]);
                 tc_commit(&t_full[buf]);
-                new_tile = ++s == K;
-                if (new_tile) s = 0;
-                if (new_tile || u + 1 == u1) tc_commit(&a_empty[as]);
+                new_tile = ++st == K32;
+                if (new_tile) st = 0;
+                if (new_tile || q + 1 == nu) tc_commit(&a_empty[as]);
+                if (++slot == NS) {
+                    slot = 0;
+                    fph ^= 1u;
+                }
+                if (++buf == NB) {
+                    buf = 0;
+                    eph ^= 1u;
+                }
             }
             if (!ok) {
                 atomicOr(&A.hdr->status, ST_TIMEOUT);
@@ -321,15 +354,36 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         const uint32_t lane_addr = static_cast<uint32_t>(quarter * 32) << 16;
         f2 acc[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
         unsigned long long cnt = 0;
-        int64_t t = u0 / K, s = u0 - (u0 / K) * K;
-        int64_t q = 0;
-        for (int64_t u = u0; u < u1; ++u, ++q) {
-            const int32_t eo0 = static_cast<int32_t>(s) * JS;
-            const int buf = static_cast<int>(q % NB);
+        int64_t t = t0;
+        int32_t st = s0;
+        int32_t buf = 0;
+        uint32_t fph = 0;   // t_full phase parity
+        for (int32_t q = 0; q < nu; ++q) {
+            const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
-            const bool got =
-                __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], static_cast<uint32_t>((q / NB) & 1),
-                                                          A.wait_ns, abort_flag));
+            bool got;
+            if constexpr (LEADER) {
+                if (ew == 0 && lane == 0) {
+                    if (mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag)) {
+                        __threadfence_block();
+                        seq[buf] = q + 1;
+                    }
+                }
+                bool seen = false;
+                const uint64_t w0 = globaltimer_ns();
+                for (;;) {
+                    if (seq[buf] >= q + 1) {
+                        seen = true;
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    if (globaltimer_ns() - w0 > A.wait_ns) break;
+                }
+                __threadfence_block();
+                got = __all_sync(0xFFFFFFFFu, seen);
+            } else {
+                got = __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
+            }
             if (!got) {
                 if (lane == 0) {
                     atomicOr(&A.hdr->status, ST_TIMEOUT);
@@ -378,8 +432,12 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     acc[a] = kAccInit;
                 }
             }
-            if (++s == K) {
-                s = 0;
+            if (++buf == NB) {
+                buf = 0;
+                fph ^= 1u;
+            }
+            if (++st == K32) {
+                st = 0;
                 ++t;
             }
         }
@@ -682,10 +740,10 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0>
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool LEADER = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, LEADER>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -703,7 +761,7 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 9) v = 0;
+        if (v < 0 || v > 12) v = 0;
     }
     return v;
 }
@@ -730,6 +788,9 @@ static cc_status tc_pick(TcLaunch &L) {
         case 7: return tc_launch_of<256, 2, 8, 12, 32>(L);
         case 8: return tc_launch_of<256, 2, 8, 12, 96>(L);
         case 9: return tc_launch_of<256, 2, 16, 12, 32>(L);
+        case 10: return tc_launch_of<256, 2, 8, 12, 0, true>(L);
+        case 11: return tc_launch_of<256, 2, 16, 12, 0, true>(L);
+        case 12: return tc_launch_of<128, 4, 8, 16, 0, true>(L);
         case 1: return tc_launch_of<128, 4, 8, 16>(L);
         case 2: return tc_launch_of<128, 4, 4, 16>(L);
         case 3: return tc_launch_of<256, 2, 16, 12>(L);
