@@ -702,8 +702,19 @@ def cpu_baseline(sets):
         oracle.count_i32(x, y, z, r2)
     dt = time.perf_counter() - t0
     tests = sum(pairs(len(s[0])) for s in sets)
+    # the literal loop on one core, on a bounded sample (the first 32768 points of the
+    # first set: 5.4e8 pair tests)
+    x, y, z, r2 = sets[0]
+    m = min(len(x), 32768)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.count_i32(x[:m], y[:m], z[:m], r2)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(0)
     return {"value": tests / dt / 1e9, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": "the full step (all three sets) once", "seconds": dt}
+            "sample": "the full step (all three sets) once", "seconds": dt,
+            "one_core": {"value": pairs(m) / dt1 / 1e9, "unit": METRIC, "cores": 1,
+                         "sample": f"first {m} points of the first set, r2 = {r2}", "seconds": dt1}}
 
 
 if __name__ == "__main__":
