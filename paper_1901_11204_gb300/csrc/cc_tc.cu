@@ -159,8 +159,7 @@ struct TcSmem {
     static constexpr int kNBars = 5 + 2 * NS + 2 * NB;
     static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
-    static constexpr int kSeq = kRed + EPW * 8;           // published unit per accumulator
-    static constexpr int kTotal = kSeq + NB * 8;
+    static constexpr int kTotal = kRed + EPW * 8;
 };
 
 __device__ __forceinline__ f2 f2_fma_rm(f2 a, f2 b, f2 c) {
@@ -183,10 +182,7 @@ __device__ __forceinline__ uint32_t acc_count(f2 a) {
 // unit, SCR are screened on the integer ALU (a three-input OR of the raw bits per two
 // values; a set sign bit sends that group to an exact recount, rare unless hits are
 // dense) and the rest counted exactly on the FP32 pipe, so the two pipes share the work.
-// LEADER: one epilogue thread polls the accumulator barrier and publishes the unit's
-// sequence number in shared memory; the other epilogue threads poll that word (plain
-// shared loads, no traffic on the barrier unit), and the copy warp waits suspended.
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool LEADER = false>
+template <int JS, int NB, int EPW, int NS, int SCR = 0>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -206,7 +202,6 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
-    volatile long long *seq = reinterpret_cast<volatile long long *>(smem + L::kSeq);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -214,7 +209,6 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
-        for (int i = 0; i < NB; ++i) seq[i] = 0;
         for (int i = 0; i < NB; ++i) {
             mbar_init(&t_full[i], 1);
             mbar_init(&t_empty[i], EPW);
@@ -268,9 +262,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     ++na;
                     cur_t = t;
                 }
-                const bool free_slot = LEADER ? mbar_wait_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)
-                                              : mbar_spin_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag);
-                if (!free_slot) break;
+                if (!mbar_spin_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)) break;
                 mbar_arrive_expect_tx(&b_full[slot], kStage);
                 bulk_g2s(sB + slot * kStage, bsrc, kStage, &b_full[slot]);
                 bsrc += JS * TC_ROW;
@@ -361,29 +353,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         for (int32_t q = 0; q < nu; ++q) {
             const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
-            bool got;
-            if constexpr (LEADER) {
-                if (ew == 0 && lane == 0) {
-                    if (mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag)) {
-                        __threadfence_block();
-                        seq[buf] = q + 1;
-                    }
-                }
-                bool seen = false;
-                const uint64_t w0 = globaltimer_ns();
-                for (;;) {
-                    if (seq[buf] >= q + 1) {
-                        seen = true;
-                        break;
-                    }
-                    if (*abort_flag) break;
-                    if (globaltimer_ns() - w0 > A.wait_ns) break;
-                }
-                __threadfence_block();
-                got = __all_sync(0xFFFFFFFFu, seen);
-            } else {
-                got = __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
-            }
+            const bool got = __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
                     atomicOr(&A.hdr->status, ST_TIMEOUT);
@@ -462,255 +432,6 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
 }
 
 // ---------------------------------------------------------------------------------------
-// split-epilogue variant: stages of 256 objects, two TMEM accumulators, and the epilogue
-// warps split by unit parity (warps 2-5 take the even units of the CTA's share, warps 6-9
-// the odd ones), each warp covering its lane quarter across all 256 columns in two
-// 128-column halves. On every SMSP one warp then counts while the other loads, instead
-// of both loading and then both counting the same unit. The j-stage ring holds pairs of
-// consecutive stages under one barrier, so the MMA lane commits the ring once per two
-// units.
-// ---------------------------------------------------------------------------------------
-
-template <int NP>
-struct TcSmem2 {
-    static constexpr int kStage = 256 * TC_ROW;           // 8 KB
-    static constexpr int kPair = 2 * kStage;              // one ring slot: two stages
-    static constexpr int kA = 0;
-    static constexpr int kB = 2 * TC_ATILE;
-    static constexpr int kBars = kB + NP * kPair;
-    // a_full[2] a_empty[2] b_full[NP] b_empty[NP] t_full[2] t_empty[2] done
-    static constexpr int kNBars = 9 + 2 * NP;
-    static constexpr int kMisc = kBars + kNBars * 8;
-    static constexpr int kRed = kMisc + 16;
-    static constexpr int kTotal = kRed + 8 * 8;
-};
-
-template <int NP>
-__global__ void __launch_bounds__(320, 1) k_pairs_tc2(TcArgs A) {
-    using L = TcSmem2<NP>;
-    constexpr int JS = 256;
-    constexpr int kStage = L::kStage;
-    extern __shared__ __align__(1024) uint8_t smem[];
-    if (A.hdr->mode != MODE_I32_TC) return;
-
-    uint8_t *sA = smem + L::kA;
-    uint8_t *sB = smem + L::kB;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
-    uint64_t *a_full = bars, *a_empty = bars + 2;
-    uint64_t *b_full = bars + 4, *b_empty = bars + 4 + NP;
-    uint64_t *t_full = bars + 4 + 2 * NP, *t_empty = t_full + 2, *done = t_full + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
-    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&a_full[i], 1);
-            mbar_init(&a_empty[i], 1);
-            mbar_init(&t_full[i], 1);
-            mbar_init(&t_empty[i], 4);   // the four warps of the buffer's group
-        }
-        for (int i = 0; i < NP; ++i) {
-            mbar_init(&b_full[i], 1);
-            mbar_init(&b_empty[i], 1);
-        }
-        mbar_init(done, 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    if (warp == 1) {
-        tmem_alloc(tmem_slot, 512);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = *tmem_slot;
-
-    const int64_t G = gridDim.x;
-    const int64_t u0 = (A.units * blockIdx.x) / G;
-    const int64_t u1 = (A.units * (blockIdx.x + 1)) / G;
-    const int64_t nu = u1 - u0;   // units of this CTA, local index q = u - u0
-    const int64_t K = A.K;
-
-    if (warp == 0) {
-        // ------------------------------- copy warp -------------------------------------
-        if (lane == 0 && !A.stall) {
-            int64_t t = u0 / K, s = u0 - (u0 / K) * K;
-            int64_t cur_t = -1;
-            uint32_t na = 0;
-            int64_t q = 0, pairs = 0;
-            bool stop = false;
-            while (q < nu && !stop) {
-                const int64_t p = q >> 1;
-                const int slot = static_cast<int>(p % NP);
-                if (!mbar_spin_bounded(&b_empty[slot], static_cast<uint32_t>(((p / NP) & 1) ^ 1), A.wait_ns,
-                                       abort_flag))
-                    break;
-                const int nst = (q + 1 < nu) ? 2 : 1;
-                mbar_arrive_expect_tx(&b_full[slot], static_cast<uint32_t>(nst * kStage));
-                ++pairs;   // armed: the abort path below waits for this slot too
-                for (int k = 0; k < nst; ++k, ++q) {
-                    if (t != cur_t) {
-                        const uint32_t as = na & 1u;
-                        if (!mbar_spin_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) {
-                            stop = true;
-                            break;
-                        }
-                        mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
-                        bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
-                        ++na;
-                        cur_t = t;
-                    }
-                    bulk_g2s(sB + slot * L::kPair + k * kStage, A.Bop + (t * TC_T + s * JS) * TC_ROW, kStage,
-                             &b_full[slot]);
-                    if (++s == K) {
-                        s = 0;
-                        ++t;
-                    }
-                }
-            }
-            if (*abort_flag || stop) {
-                // wait (bounded) for the copies of the last ring slots and i-tile slots
-                for (int64_t pp = pairs > NP ? pairs - NP : 0; pp < pairs; ++pp)
-                    (void)mbar_wait_bounded(&b_full[pp % NP], static_cast<uint32_t>((pp / NP) & 1), A.wait_ns);
-                for (uint32_t k = (na > 2 ? na - 2 : 0); k < na; ++k)
-                    (void)mbar_wait_bounded(&a_full[k & 1u], (k >> 1) & 1u, A.wait_ns);
-            }
-        }
-    } else if (warp == 1) {
-        // ------------------------------- MMA lane --------------------------------------
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32_f32(TC_T, JS);
-            int64_t s = u0 - (u0 / K) * K;
-            bool new_tile = true;
-            uint32_t na = 0;
-            bool ok = true;
-            for (int64_t q = 0; q < nu; ++q) {
-                if (new_tile) {
-                    ok = mbar_spin_bounded(&a_full[na & 1u], (na >> 1) & 1u, A.wait_ns, abort_flag);
-                    if (!ok) break;
-                    ++na;
-                }
-                const uint32_t as = (na - 1) & 1u;
-                const int64_t p = q >> 1;
-                const int slot = static_cast<int>(p % NP);
-                const int buf = static_cast<int>(q & 1);
-                if ((q & 1) == 0) {
-                    ok = mbar_spin_bounded(&b_full[slot], static_cast<uint32_t>((p / NP) & 1), A.wait_ns, abort_flag);
-                    if (!ok) break;
-                }
-                ok = mbar_spin_bounded(&t_empty[buf], static_cast<uint32_t>(((q >> 1) & 1) ^ 1), A.wait_ns,
-                                       abort_flag);
-                if (!ok) break;
-                tc_fence_after();
-                const uint64_t ad = smem_desc_k_noswizzle(smem_u32(sA + as * TC_ATILE), 128, 256);
-                const uint64_t bd =
-                    smem_desc_k_noswizzle(smem_u32(sB + slot * L::kPair + (q & 1) * kStage), 128, 256);
-                tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad, bd, idesc, 0u);
-                tc_commit(&t_full[buf]);
-                if ((q & 1) == 1 || q + 1 == nu) tc_commit(&b_empty[slot]);
-                new_tile = ++s == K;
-                if (new_tile) s = 0;
-                if (new_tile || q + 1 == nu) tc_commit(&a_empty[as]);
-            }
-            if (!ok) {
-                atomicOr(&A.hdr->status, ST_TIMEOUT);
-                *abort_flag = 1;
-            }
-            tc_commit(done);
-            if (!mbar_wait_bounded(done, 0u, A.wait_ns)) atomicOr(&A.hdr->status, ST_TIMEOUT);
-        }
-    } else {
-        // ------------------------------- epilogue warps --------------------------------
-        const int ew = warp - 2;
-        const int grp = ew >> 2;               // units q with q % 2 == grp, accumulator grp
-        const int quarter = warp & 3;
-        const int row = quarter * 32 + lane;
-        const uint32_t taddr0 = tbase + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(grp * JS);
-        f2 acc[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
-        unsigned long long cnt = 0;
-        int64_t t = (u0 + grp) / K, s = (u0 + grp) - ((u0 + grp) / K) * K;
-        int64_t k = 0;   // units of this group done
-        for (int64_t q = grp; q < nu; q += 2, ++k) {
-            const int32_t eo0 = static_cast<int32_t>(s) * JS;
-            const bool got =
-                __shfl_sync(0xFFFFFFFFu,
-                            lane == 0 ? static_cast<int>(mbar_spin_bounded(&t_full[grp], static_cast<uint32_t>(k & 1),
-                                                                           A.wait_ns, abort_flag))
-                                      : 0,
-                            0) != 0;
-            if (!got) {
-                if (lane == 0) {
-                    atomicOr(&A.hdr->status, ST_TIMEOUT);
-                    *abort_flag = 1;
-                }
-                break;
-            }
-            tc_fence_after();
-            const bool full = eo0 >= TC_T && eo0 + JS - 1 <= A.h;
-            const int64_t i = t * TC_T + row;
-            const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t v[128];
-                tmem_ld128(taddr0 + half * 128, v);
-                if (half == 1) {
-                    // both halves read: return the accumulator before counting the second
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&t_empty[grp]);
-                }
-                if (full) {
-#pragma unroll
-                    for (int j = 0; j < 64; ++j) {
-                        const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
-                        acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
-                    }
-                } else {
-                    const int64_t d0 = static_cast<int64_t>(eo0) + half * 128 - row;   // e - i of column 0
-#pragma unroll
-                    for (int j = 0; j < 128; ++j)
-                        cnt += (d0 + j >= 1 && d0 + j <= ev && __uint_as_float(v[j]) < 0.0f) ? 1u : 0u;
-                }
-            }
-            if ((k & 511) == 511) {
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    cnt += acc_count(acc[a]);
-                    acc[a] = kAccInit;
-                }
-            }
-            // advance two units
-            s += 2;
-            while (s >= K) {
-                s -= K;
-                ++t;
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) cnt += acc_count(acc[a]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
-        if (lane == 0) red[ew] = cnt;
-    }
-
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tbase, 512);
-    }
-    if (threadIdx.x == 0) {
-        unsigned long long c = 0;
-        for (int i = 0; i < 8; ++i) c += red[i];
-        if (c && A.d_count) atomicAdd(A.d_count, c);
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 
@@ -740,10 +461,10 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool LEADER = false>
+template <int JS, int NB, int EPW, int NS, int SCR = 0>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, LEADER>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -761,40 +482,18 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 12) v = 0;
+        if (v < 0 || v > 5) v = 0;
     }
     return v;
 }
 
-template <int NP>
-static cc_status tc2_launch_of(TcLaunch &L) {
-    static_assert(TcSmem2<NP>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc2<NP>;
-    static bool attr = false;
-    if (!attr) {
-        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
-        attr = true;
-    }
-    L.fn = reinterpret_cast<const void *>(fn);
-    L.js = 256;
-    L.threads = 320;
-    return CC_OK;
-}
-
 static cc_status tc_pick(TcLaunch &L) {
     switch (tc_variant()) {
-        case 5: return tc2_launch_of<6>(L);
-        case 6: return tc_launch_of<256, 2, 8, 12, 64>(L);
-        case 7: return tc_launch_of<256, 2, 8, 12, 32>(L);
-        case 8: return tc_launch_of<256, 2, 8, 12, 96>(L);
-        case 9: return tc_launch_of<256, 2, 16, 12, 32>(L);
-        case 10: return tc_launch_of<256, 2, 8, 12, 0, true>(L);
-        case 11: return tc_launch_of<256, 2, 16, 12, 0, true>(L);
-        case 12: return tc_launch_of<128, 4, 8, 16, 0, true>(L);
         case 1: return tc_launch_of<128, 4, 8, 16>(L);
         case 2: return tc_launch_of<128, 4, 4, 16>(L);
         case 3: return tc_launch_of<256, 2, 16, 12>(L);
         case 4: return tc_launch_of<128, 4, 16, 16>(L);
+        case 5: return tc_launch_of<256, 2, 8, 12, 64>(L);
         default: return tc_launch_of<256, 2, 8, 12>(L);
     }
 }
