@@ -182,7 +182,13 @@ __device__ __forceinline__ uint32_t acc_count(f2 a) {
 // unit, SCR are screened on the integer ALU (a three-input OR of the raw bits per two
 // values; a set sign bit sends that group to an exact recount, rare unless hits are
 // dense) and the rest counted exactly on the FP32 pipe, so the two pipes share the work.
-template <int JS, int NB, int EPW, int NS, int SCR = 0>
+// PRE: the MMA thread tests the next unit's barriers right after issuing the current
+// MMA, before its commits. STEW: the first epilogue thread, not the MMA thread, returns
+// each j-stage slot and each i-tile slot (plain arrivals once it has seen the completion
+// of the MMAs that read them), leaving the MMA thread one commit per unit. The MMA
+// thread is the pipeline's critical path (it shares its SMSP with two counting warps);
+// both measured faster and are on in the default shape.
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -302,6 +308,9 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             uint32_t fph = 0;   // b_full phase parity
             uint32_t eph = 1;   // t_empty phase parity to wait for (first pass: free)
             bool ok = true;
+            // outcome of the next unit's two barrier tests, taken early (right after the
+            // previous MMA) so that their latency overlaps the commits
+            bool pre_full = false, pre_empty = false;
             for (int32_t q = 0; q < nu; ++q) {
                 if (new_tile) {
                     ok = mbar_spin_bounded(&a_full[na & 1u], (na >> 1) & 1u, A.wait_ns, abort_flag);
@@ -309,17 +318,15 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     ++na;
                 }
                 const uint32_t as = (na - 1) & 1u;
-                ok = mbar_spin_bounded(&b_full[slot], fph, A.wait_ns, abort_flag) &&
-                     mbar_spin_bounded(&t_empty[buf], eph, A.wait_ns, abort_flag);
+                ok = (pre_full || mbar_spin_bounded(&b_full[slot], fph, A.wait_ns, abort_flag)) &&
+                     (pre_empty || mbar_spin_bounded(&t_empty[buf], eph, A.wait_ns, abort_flag));
                 if (!ok) break;
                 tc_fence_after();
                 tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad0 + as * (TC_ATILE >> 4),
                             bd0 + static_cast<uint32_t>(slot) * (kStage >> 4), idesc, 0u);
-                tc_commit(&b_empty[slot]);
-                tc_commit(&t_full[buf]);
+                const int32_t cslot = slot, cbuf = buf;
                 new_tile = ++st == K32;
                 if (new_tile) st = 0;
-                if (new_tile || q + 1 == nu) tc_commit(&a_empty[as]);
                 if (++slot == NS) {
                     slot = 0;
                     fph ^= 1u;
@@ -328,6 +335,13 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     buf = 0;
                     eph ^= 1u;
                 }
+                if (PRE) {
+                    pre_full = mbar_test_wait(&b_full[slot], fph);
+                    pre_empty = mbar_test_wait(&t_empty[buf], eph);
+                }
+                if (!STEW) tc_commit(&b_empty[cslot]);
+                tc_commit(&t_full[cbuf]);
+                if (!STEW && (new_tile || q + 1 == nu)) tc_commit(&a_empty[as]);
             }
             if (!ok) {
                 atomicOr(&A.hdr->status, ST_TIMEOUT);
@@ -350,6 +364,8 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         int32_t st = s0;
         int32_t buf = 0;
         uint32_t fph = 0;   // t_full phase parity
+        int32_t rslot = 0;  // j-stage ring slot of unit q
+        uint32_t tord = 0;  // ordinal of unit q's tile in this share (i-tile slot tord & 1)
         for (int32_t q = 0; q < nu; ++q) {
             const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
@@ -360,6 +376,12 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     *abort_flag = 1;
                 }
                 break;
+            }
+            if (STEW && ew == 0 && lane == 0) {
+                // unit q's MMA (and every earlier one) is complete: its j-stage slot, and
+                // after the share's last unit of a tile the i-tile slot, can be refilled
+                mbar_arrive(&b_empty[rslot]);
+                if (st == K32 - 1 || q + 1 == nu) mbar_arrive(&a_empty[tord & 1u]);
             }
             tc_fence_after();
             uint32_t v[CPW];
@@ -406,9 +428,11 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 buf = 0;
                 fph ^= 1u;
             }
+            if (++rslot == NS) rslot = 0;
             if (++st == K32) {
                 st = 0;
                 ++t;
+                ++tord;
             }
         }
 #pragma unroll
@@ -461,10 +485,10 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0>
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -482,19 +506,18 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 5) v = 0;
+        if (v < 0 || v > 4) v = 0;
     }
     return v;
 }
 
 static cc_status tc_pick(TcLaunch &L) {
     switch (tc_variant()) {
-        case 1: return tc_launch_of<128, 4, 8, 16>(L);
-        case 2: return tc_launch_of<128, 4, 4, 16>(L);
-        case 3: return tc_launch_of<256, 2, 16, 12>(L);
-        case 4: return tc_launch_of<128, 4, 16, 16>(L);
-        case 5: return tc_launch_of<256, 2, 8, 12, 64>(L);
-        default: return tc_launch_of<256, 2, 8, 12>(L);
+        case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
+        case 2: return tc_launch_of<128, 4, 8, 16, 0, true, true>(L);
+        case 3: return tc_launch_of<256, 2, 16, 12, 0, true, true>(L);
+        case 4: return tc_launch_of<256, 2, 8, 12, 64, true, true>(L);
+        default: return tc_launch_of<256, 2, 8, 12, 0, true, true>(L);
     }
 }
 
