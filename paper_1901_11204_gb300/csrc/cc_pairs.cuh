@@ -5,6 +5,12 @@
 
 #include "cc_internal.cuh"
 
+// FP32 sphere predicate on packed FP32x2 registers (two pairs per instruction); 0 selects
+// the scalar form.
+#ifndef CC_F32_PACKED
+#define CC_F32_PACKED 1
+#endif
+
 namespace cc {
 
 struct __align__(16) Rec {
@@ -56,6 +62,26 @@ __device__ __forceinline__ uint32_t sphere_hit(float xi, float yi, float zi, flo
     const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
     const float s = __fadd_rn(ri, rj);
     return d2 <= __fmul_rn(s, s) ? 1u : 0u;
+}
+
+// The same predicate for two pairs at once on packed FP32x2 registers. The squares are
+// fma.rn(d, d, +0): exactly RN(d*d) (the product is never negative, and +0 + RN(p) =
+// RN(p)), but, unlike a multiply, an FMA is never contracted into the following add, so
+// every operation keeps the specified rounding. (An FMA with a +0 addend cannot be
+// rewritten as a multiply either: for d = -0 the sum is +0.)
+__device__ __forceinline__ f2 f2_sq_rn(f2 v) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(v), "l"(0ull));
+    return d;
+}
+
+__device__ __forceinline__ void sphere_hit2(f2 xi, f2 yi, f2 zi, f2 ri, f2 xj, f2 yj, f2 zj, f2 rj, uint32_t &h0,
+                                            uint32_t &h1) {
+    const f2 d2 = f2_add(f2_add(f2_sq_rn(f2_sub(xi, xj)), f2_sq_rn(f2_sub(yi, yj))), f2_sq_rn(f2_sub(zi, zj)));
+    const f2 s = f2_add(ri, rj);
+    const f2 s2 = f2_mul(s, s);
+    h0 = f2_lo(d2) <= f2_lo(s2) ? 1u : 0u;
+    h1 = f2_hi(d2) <= f2_hi(s2) ? 1u : 0u;
 }
 
 __device__ __forceinline__ uint32_t wide_d2(float xi, float yi, float zi, float xj, float yj, float zj) {
@@ -181,9 +207,13 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
                 h0 = sign_lo(v);
                 h1 = sign_hi(v);
             } else if (MODE == MODE_F32) {
+#if CC_F32_PACKED
+                sphere_hit2(s.a[r], s.b[r], s.c[r], s.d[r], p0.x, p0.y, p1.x, p1.y, h0, h1);
+#else
                 const float xi = f2_lo(s.a[r]), yi = f2_lo(s.b[r]), zi = f2_lo(s.c[r]), ri = f2_lo(s.d[r]);
                 h0 = sphere_hit(xi, yi, zi, ri, f2_lo(p0.x), f2_lo(p0.y), f2_lo(p1.x), f2_lo(p1.y));
                 h1 = sphere_hit(xi, yi, zi, ri, f2_hi(p0.x), f2_hi(p0.y), f2_hi(p1.x), f2_hi(p1.y));
+#endif
             } else {
                 h0 = wide_d2(f2_lo(s.a[r]), f2_lo(s.b[r]), f2_lo(s.c[r]), f2_lo(p0.x), f2_lo(p0.y),
                              f2_lo(p1.x)) <= r2 ? 1u : 0u;
