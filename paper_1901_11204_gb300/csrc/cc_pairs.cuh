@@ -186,6 +186,33 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
                 }
             }
         }
+    } else if (MODE == MODE_F32 && CC_F32_PACKED && !MASKED && !SUM) {
+        // Unmasked FP32 spheres, object-outer over blocks of QB staged record pairs (the
+        // object's coordinates are the operand repeated by consecutive instructions).
+        constexpr int QB = 4;
+#pragma unroll 1
+        for (int q0 = 0; q0 < JS / 2; q0 += QB) {
+            f2 X[QB], Y[QB], Z[QB], W[QB];
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                const ulonglong2 p0 = st[2 * (q0 + q)];
+                const ulonglong2 p1 = st[2 * (q0 + q) + 1];
+                X[q] = p0.x;
+                Y[q] = p0.y;
+                Z[q] = p1.x;
+                W[q] = p1.y;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+#pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    uint32_t h0, h1;
+                    sphere_hit2(s.a[r], s.b[r], s.c[r], s.d[r], X[q], Y[q], Z[q], W[q], h0, h1);
+                    cr[r] += h0;
+                    cr[r] += h1;
+                }
+            }
+        }
     } else {
     // Groups of up to 64 record pairs; with SUM, the groups that produced a hit are
     // marked in a 64-bit mask and their interaction terms are added after the group, so
