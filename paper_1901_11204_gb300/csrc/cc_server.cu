@@ -36,6 +36,11 @@ struct SetDescHost {   // layout identical to the device SetDesc of the batching
 
 cc_status plan_launch_sets(cc_plan *P, int32_t n_sets, int32_t want_sum, unsigned long long *d_counts,
                            float *d_sums, cudaStream_t s);
+size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc);
+bool tc_enabled();
+// Integer sets at least this large have their count queries served by the single-set
+// path (the tensor-core kernel when the set's range admits it) instead of the batch.
+constexpr int64_t kServerTcMinN = 16384;
 void *plan_sets_buffer_v(cc_plan *P);
 size_t plan_set_desc_bytes();
 
@@ -65,6 +70,7 @@ struct SetRec {
     size_t bytes = 0;
     int32_t refs = 0;
     bool alive = false;
+    bool single = false;    // count queries go to the single-set (tensor-core) path
 };
 
 struct Lane {
@@ -95,6 +101,7 @@ struct cc_server {
     std::vector<SetRec> sets;
     size_t resident_bytes = 0;
     size_t inflight_bytes = 0;
+    size_t single_ws_reserved = 0;   // budget held for the lanes' single-set workspaces
     int64_t inflight = 0;
     int64_t submitted = 0;
     int64_t finished = 0;
@@ -104,7 +111,7 @@ struct cc_server {
     bool stop = false;
     int device = 0;
     // stats
-    int64_t batches = 0, admitted = 0, peak_inflight = 0;
+    int64_t batches = 0, admitted = 0, peak_inflight = 0, single_launches = 0;
     int64_t peak_bytes = 0;
     std::string sched_error;
 };
@@ -178,6 +185,7 @@ static bool launch(cc_server *S, Lane &L) {
         S->peak_inflight = std::max(S->peak_inflight, S->inflight);
         S->peak_bytes = std::max<int64_t>(S->peak_bytes, static_cast<int64_t>(S->resident_bytes + S->inflight_bytes));
         bool any_sum = false;
+        std::vector<int32_t> singles;   // batch entries served by the single-set path
         for (size_t k = 0; k < batch.size(); ++k) {
             const SetRec &sr = S->sets[batch[k].set_id];
             SetDescHost d;
@@ -189,6 +197,10 @@ static bool launch(cc_server *S, Lane &L) {
             d.n = sr.n;
             d.dtype = sr.dtype;
             d.r2 = batch[k].r2;
+            if (sr.single && batch[k].op == CC_OP_COUNT) {
+                d.n = 0;   // the batch writes 0; the single-set call below writes the count
+                singles.push_back(static_cast<int32_t>(k));
+            }
             L.h_sets[k] = d;
             any_sum = any_sum || batch[k].op == CC_OP_SUM;
         }
@@ -201,6 +213,21 @@ static bool launch(cc_server *S, Lane &L) {
         cc_status st = e == cudaSuccess
                            ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
                            : CC_ERR_CUDA;
+        // large integer count queries: one single-set call each, stream-ordered after the
+        // batch (this thread is the lane stream's only user, so its workspace is too)
+        for (size_t j = 0; st == CC_OK && j < singles.size(); ++j) {
+            const int32_t k = singles[j];
+            const SetRec &sr = S->sets[L.batch[k].set_id];
+            const size_t col = static_cast<size_t>(sr.n) * 4;
+            cc_points pts;
+            pts.dtype = CC_I32;
+            pts.x = sr.buf;
+            pts.y = static_cast<char *>(sr.buf) + col;
+            pts.z = static_cast<char *>(sr.buf) + 2 * col;
+            pts.r = nullptr;
+            st = cc_count_pairs(&pts, sr.n, L.batch[k].r2, L.d_counts + k, L.stream);
+            S->single_launches += 1;
+        }
         if (st == CC_OK) e = cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(unsigned long long) * nb,
                                              cudaMemcpyDeviceToHost, L.stream);
         if (st == CC_OK && e == cudaSuccess && any_sum)
@@ -286,11 +313,23 @@ cc_status cc_server_register_set(cc_server *S, const cc_points *p, int64_t n, in
     const int cols = p->dtype == CC_F32 ? 4 : 3;
     const size_t col = static_cast<size_t>(n) * 4;
     const size_t bytes = std::max<size_t>(col * cols, 16);
+    bool single = false;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->resident_bytes + S->inflight_bytes + bytes > S->budget)
             return fail(CC_ERR_NOMEM, "memory budget exceeded by this set");
         S->resident_bytes += bytes;
+        if (p->dtype == CC_I32 && n >= kServerTcMinN && tc_enabled()) {
+            // both lanes may hold a workspace of this size (allocated by the scheduler on
+            // first use); without room in the budget the set stays on the batched path
+            const size_t need = 2 * single_ws_bytes(n, false, true);
+            const size_t extra = need > S->single_ws_reserved ? need - S->single_ws_reserved : 0;
+            if (S->resident_bytes + S->inflight_bytes + extra <= S->budget) {
+                S->resident_bytes += extra;
+                S->single_ws_reserved += extra;
+                single = true;
+            }
+        }
     }
     void *buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, bytes);
@@ -316,6 +355,7 @@ cc_status cc_server_register_set(cc_server *S, const cc_points *p, int64_t n, in
     r.dtype = p->dtype;
     r.bytes = bytes;
     r.alive = true;
+    r.single = single;
     S->sets.push_back(r);
     *set_id = static_cast<int32_t>(S->sets.size() - 1);
     S->peak_bytes = std::max<int64_t>(S->peak_bytes, static_cast<int64_t>(S->resident_bytes + S->inflight_bytes));

@@ -127,3 +127,30 @@ def test_cfg5_pool_sample(cc):
         if op == cc.CC_OP_SUM:
             assert abs(res[k]["sum"] - want[1]) <= 1e-5 * max(abs(want[1]), 1e-30)
     srv.close()
+
+
+def test_large_integer_sets_in_the_mix(cc):
+    """Integer sets of n >= 16384: their count queries run the single-set (tensor-core)
+    path stream-ordered after the batch, their sum queries stay in the batch; every result
+    equals the oracle, alone and mixed with small sets and FP32 spheres."""
+    rng = np.random.default_rng(21)
+    sets = []
+    for n, box in ((20000, 200), (30001, 1024), (16384, 64)):
+        x, y, z = (rng.integers(0, box, n).astype(np.int32) for _ in range(3))
+        sets.append(("i32", x, y, z, None))
+    sets += pool(k=8, seed=22)
+    srv = cc.Server(1 << 30, 64)
+    ids = [srv.register_set(*s[1:4], r=s[4]) for s in sets]
+    reqs = []
+    for k, sid in enumerate(ids):
+        reqs.append((sid, cc.CC_OP_COUNT, 9, 2 * k))
+        if sets[k][0] == "i32" and len(sets[k][1]) >= 16384:
+            reqs.append((sid, cc.CC_OP_SUM, 9, 2 * k + 1))
+    res = run_requests(srv, reqs)
+    res2 = run_requests(srv, [(a, b, c, d + 10000) for (a, b, c, d) in reqs])
+    for (sid, op, r2, rid) in reqs:
+        k = rid // 2
+        want_c, _ = expected(sets[k], 9)
+        assert res[rid]["status"] == 0 and res[rid]["count"] == want_c, (k, op)
+        assert res2[rid + 10000]["count"] == want_c
+    srv.close()
