@@ -135,11 +135,21 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, Se
         st->cursor = 0;
         st->status = 0;
     }
+    // the offsets of this warp's next set are loaded while the current one is reduced
+    int64_t na = 0, nb = 0;
+    if (P->offsets && warp < S) {
+        na = P->offsets[warp];
+        nb = P->offsets[warp + 1];
+    }
     for (int64_t k = warp; k < S; k += nwarps) {
         SetDesc d;
         uint32_t flag = SET_OK;
         if (P->offsets) {
-            const int64_t a = P->offsets[k], b = P->offsets[k + 1];
+            const int64_t a = na, b = nb;
+            if (k + nwarps < S) {
+                na = P->offsets[k + nwarps];
+                nb = P->offsets[k + nwarps + 1];
+            }
             const size_t es = 4;
             d.x = static_cast<const char *>(P->pts.x) + a * es;
             d.y = static_cast<const char *>(P->pts.y) + a * es;
@@ -163,12 +173,41 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, Se
             uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0, 0, 0};
             const int32_t *c[3] = {static_cast<const int32_t *>(d.x), static_cast<const int32_t *>(d.y),
                                    static_cast<const int32_t *>(d.z)};
-            for (int64_t i = lane; i < d.n; i += 32)
-                for (int a = 0; a < 3; ++a) {
-                    const uint32_t u = ord_enc(c[a][i]);
-                    mn[a] = min(mn[a], u);
-                    mx[a] = max(mx[a], u);
-                }
+            // four elements per lane per step, all loads issued before the reductions (a
+            // set of up to 128 objects costs one memory latency)
+            int64_t i = lane;
+            for (; i + 96 < d.n; i += 128) {
+                uint32_t u[3][4];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) u[a][e] = ord_enc(c[a][i + 32 * e]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        mn[a] = min(mn[a], u[a][e]);
+                        mx[a] = max(mx[a], u[a][e]);
+                    }
+            }
+            {
+                uint32_t u[3][4];
+                bool ok[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) ok[e] = i + 32 * e < d.n;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) u[a][e] = ok[e] ? ord_enc(c[a][i + 32 * e]) : 0u;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (ok[e]) {
+                            mn[a] = min(mn[a], u[a][e]);
+                            mx[a] = max(mx[a], u[a][e]);
+                        }
+            }
             int64_t m = 0, dmax = 0, lo[3], span[3];
             for (int a = 0; a < 3; ++a) {
                 mn[a] = __reduce_min_sync(0xFFFFFFFFu, mn[a]);
@@ -478,7 +517,10 @@ __device__ __forceinline__ void run_item_r(const SetDesc &d, const SetAux &x, co
     }
 }
 
-__global__ void __launch_bounds__(kMainWarps * 32) k_b_main(const BatchParams *__restrict__ P,
+// MINB: resident CTAs per SM the register allocation must allow (the items are small, so
+// more warps in flight hide more of their load latency).
+template <int MINB>
+__global__ void __launch_bounds__(kMainWarps * 32, MINB) k_b_main(const BatchParams *__restrict__ P,
                                                            const SetDesc *sets, const SetAux *aux,
                                                            const BandTable *bt, const Item *items,
                                                            BatchState *st, unsigned long long *pcnt,
@@ -641,8 +683,26 @@ struct cc_plan {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     int main_grid = 0;
+    const void *main_fn = nullptr;   // k_b_main instance (resident CTAs per SM)
     std::mutex mu;
 };
+
+// k_b_main instance: CC_BMAIN_MINB (1..4) for sweeps, else the measured best.
+static const void *main_kernel() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("CC_BMAIN_MINB");
+        v = e ? atoi(e) : 0;
+    }
+    // measured on config 4 (100k small sets): 1 -> 0.57 ms, 2 -> 0.40, 3 -> 0.38, 4 -> 0.38
+    // (4 spills heavily in the wide bands; 3 is the default)
+    switch (v) {
+        case 1: return reinterpret_cast<const void *>(k_b_main<1>);
+        case 2: return reinterpret_cast<const void *>(k_b_main<2>);
+        case 4: return reinterpret_cast<const void *>(k_b_main<4>);
+        default: return reinterpret_cast<const void *>(k_b_main<3>);
+    }
+}
 
 static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
     const int sms = sm_count();
@@ -651,8 +711,11 @@ static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
     k_b_scan1<<<P->scan_blocks, kScanBlock, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum);
     k_b_scan2<<<1, kScanBlock, 0, s>>>(P->d_bsum, P->scan_blocks, P->d_state, P->item_cap);
     k_b_emit<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_items, P->d_state);
-    k_b_main<<<P->main_grid, kMainWarps * 32, 0, s>>>(P->d_params, P->d_sets, P->d_aux, P->d_bands, P->d_items,
-                                                       P->d_state, P->d_pcnt, P->d_psum);
+    {
+        void *args[] = {&P->d_params, &P->d_sets, &P->d_aux, &P->d_bands, &P->d_items,
+                        &P->d_state, &P->d_pcnt, &P->d_psum};
+        CC_CUDA(cudaLaunchKernel(P->main_fn, dim3(P->main_grid), dim3(kMainWarps * 32), args, 0, s));
+    }
     k_b_finish<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_flags, P->d_state,
                                        P->d_pcnt, P->d_psum);
     CC_CUDA(cudaGetLastError());
@@ -744,7 +807,8 @@ cc_status cc_plan_create(cc_plan **plan, const char *tune_table_json, int32_t ma
         return fail(CC_ERR_NOMEM, std::string("plan allocation: ") + cudaGetErrorString(e));
     }
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_b_main, kMainWarps * 32, 0);
+    P->main_fn = main_kernel();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, P->main_fn, kMainWarps * 32, 0);
     P->main_grid = sm_count() * std::max(bps, 1);
     *plan = P;
     return CC_OK;
