@@ -530,11 +530,15 @@ __global__ void __launch_bounds__(kMainWarps * 32, MINB) k_b_main(const BatchPar
     Rec *slot = slots[threadIdx.x >> 5];
     const int64_t total = st->total_items;
     const bool want_sum = P->want_sum != 0;
+    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(&st->cursor);
+    // the next item's index is taken before the current item is worked on, so the
+    // atomic's round trip overlaps the work
+    int64_t next = 0;
+    if (lane == 0) next = static_cast<int64_t>(atomicAdd(cursor, 1ull));
     for (;;) {
-        int64_t it = 0;
-        if (lane == 0) it = static_cast<int64_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&st->cursor), 1ull));
-        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        const int64_t it = __shfl_sync(0xFFFFFFFFu, next, 0);
         if (it >= total) break;
+        if (lane == 0) next = static_cast<int64_t>(atomicAdd(cursor, 1ull));
         const Item item = items[it];
         const SetDesc d = sets[item.set];
         const SetAux x = aux[item.set];
