@@ -208,8 +208,7 @@ __device__ __forceinline__ uint32_t stage_run(const IState<R> &s, const ulonglon
                 for (int q = 0; q < QB; ++q) {
                     uint32_t h0, h1;
                     sphere_hit2(s.a[r], s.b[r], s.c[r], s.d[r], X[q], Y[q], Z[q], W[q], h0, h1);
-                    cr[r] += h0;
-                    cr[r] += h1;
+                    cr[r] += h0 + h1;   // one three-input integer add for both pairs
                 }
             }
         }

@@ -26,10 +26,12 @@
 //                 and every j-stage operand (256 rows, 8 KB) into an NS-deep ring,
 //   warp 1        allocates 512 TMEM columns; its lane 0 issues one
 //                 tcgen05.mma (M=128, N=256, K=8) per unit into one of two TMEM
-//                 accumulators and commits to the ring / accumulator barriers,
+//                 accumulators and commits to that accumulator's barrier,
 //   warps 2..     (EPW warps) read the accumulator rows of their TMEM lane quarter
 //                 (tcgen05.ld 32x32b) and count; stages that touch the ends of the
-//                 cyclic range take the per-pair validity mask.
+//                 cyclic range take the per-pair validity mask. The first of them also
+//                 returns each j-stage slot and i-tile slot to the copy warp once it has
+//                 seen the MMAs that read them complete.
 // Every wait is bounded by the global timer; on expiry the kernel records ST_TIMEOUT,
 // lets the other roles stop, waits (bounded) for its MMAs, frees TMEM and returns.
 #include <cuda_runtime.h>
