@@ -235,6 +235,12 @@ TC_FLOPS_PER_PAIR = 16
 TF32_PER_BF16 = 1.1 / 2.25
 
 
+def issue_roofline(sms: int, mhz: float, instr_per_pair: int) -> float:
+    """Pair tests/s (in G) at one warp-instruction per clock per SMSP and the stated
+    thread-instructions per pair test."""
+    return sms * 4 * 32 * mhz * 1e6 / instr_per_pair / 1e9
+
+
 def roofline_peak_f32(sms: int, mhz: float) -> float:
     """FP32 sphere predicate: 10 FP32-pipe operations per pair (3 sub, 3 mul, 2 add,
     radius add, radius square)."""
@@ -365,6 +371,15 @@ def main():
         }
     if achieved and clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / fmax)
+    # The pair-test roofline in which the work is stated: SMs x 4 SMSPs x 32 lanes x f_SM
+    # / 8 thread-instructions per integer pair test (3 sub, 3 mul/mad, compare,
+    # accumulate) at one warp-instruction per clock per SMSP.
+    issue_peak = issue_roofline(sms, fmax, 8)
+    issue_roofline_line = {
+        "bound": "issue", "peak": issue_peak, "unit": METRIC, "achieved": pair_rate,
+        "frac": (pair_rate / issue_peak) if pair_rate else None,
+        "peak_basis": f"{sms} SMs x 4 SMSPs x 32 lanes x {fmax:.0f} MHz / 8 thread-instructions per int pair test",
+    }
 
     # ---- end to end through the C ABI from host buffers -------------------------------
     hsets = [tuple(torch.from_numpy(a).pin_memory() for a in s[:3]) for s in sets]
@@ -412,6 +427,7 @@ def main():
                    "pair_tests_per_step": tests_per_step, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent sets per GPU)"},
         "roofline": roofline,
+        "issue_roofline": issue_roofline_line,
         "e2e": e2e,
         # per count: reset, min/max + mode, record fill, operand fill, tensor-core kernel and
         # FP32-pipe kernel (the kernel and fill of the mode not chosen return at once)
@@ -505,6 +521,8 @@ def bench_f32(cc, torch, dev, sms, fmax, peak_src):
             "sum_ms": ms_s, "sum_gpairs_s": pairs(n) / (ms_s * 1e-3) / 1e9,
             "count": cc.as_u64(cnt), "sum": float(s.item()),
             "roofline_peak": peak, "count_frac": g_count / peak,
+            "issue_roofline_peak": issue_roofline(sms, fmax, 12),
+            "count_frac_of_issue_roofline": g_count / issue_roofline(sms, fmax, 12),
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src}) / 10 FP32 ops per pair"}
 
 
