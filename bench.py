@@ -255,7 +255,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-sample", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip f32/batched/serving/cpu legs")
-    ap.add_argument("--serving-queries", type=int, default=20000)
+    ap.add_argument("--serving-queries", type=int, default=50000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
