@@ -442,6 +442,7 @@ def main():
         line["fp32_pipe_step"] = bench_fp32_pipe_step(cc, torch, step, outs, want, tests_per_step,
                                                       roofline_peak_int(sms, fmax) / 1e9, flush)
         line["f32_spheres"] = bench_f32(cc, torch, dev, sms, fmax, peak_src)
+        line["i32_sums"] = bench_i32_sums(cc, torch, dev)
         line["batched"] = bench_batched(cc, torch, dev)
         line["serving"] = bench_serving(cc, torch, dev, args.serving_queries)
         line["schedule_comparison"] = bench_schedules(cc, torch, dev)
@@ -524,6 +525,33 @@ def bench_f32(cc, torch, dev, sms, fmax, peak_src):
             "issue_roofline_peak": issue_roofline(sms, fmax, 12),
             "count_frac_of_issue_roofline": g_count / issue_roofline(sms, fmax, 12),
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src}) / 10 FP32 ops per pair"}
+
+
+def bench_i32_sums(cc, torch, dev, n=262144):
+    """Interaction sums of integer points on both kernels (tensor-core and FP32 pipe),
+    on the headline workload's first set at two hit densities."""
+    c = synth.cfg2(n)
+    t = [torch.from_numpy(c[k]).to(dev) for k in ("x", "y", "z")]
+    out = {"workload": f"N={n} int32 points uniform in [0,1024)^3"}
+    for r2 in (9, 400):
+        row = {}
+        for tc in (True, False):
+            cc.set_tensor_cores(tc)
+            try:
+                ms = _time(lambda: cc.interaction_sum(t[0], t[1], t[2], r2=r2), 10, torch)
+                s, cnt = cc.interaction_sum(t[0], t[1], t[2], r2=r2)
+                torch.cuda.synchronize()
+                mode = cc.stream_mode()
+            finally:
+                cc.set_tensor_cores(True)
+            row["tensor" if tc else "fp32_pipe"] = {
+                "sum_ms": ms, "sum_gpairs_s": pairs(n) / (ms * 1e-3) / 1e9, "mode": mode,
+                "count": cc.as_u64(cnt), "sum": float(s.item())}
+        a, b = row["tensor"], row["fp32_pipe"]
+        row["counts_equal"] = a["count"] == b["count"]
+        row["sum_rel_diff"] = abs(a["sum"] - b["sum"]) / max(abs(b["sum"]), 1e-30)
+        out[f"r2={r2}"] = row
+    return out
 
 
 def bench_linear(cc, torch, dev, peaks):

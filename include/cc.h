@@ -85,7 +85,9 @@ cc_status cc_count_pairs(const cc_points *p, int64_t n, uint32_t r2,
 
 /* Interaction sum over the colliding pairs, written to d_sum[0] (device, FP32); the
  * count of colliding pairs goes to d_count[0] when d_count is not NULL. For CC_I32 the
- * distance is sqrtf((float)d2) of the exact integer d2. */
+ * distance is sqrtf((float)d2) of the exact integer d2 and each term 1/max(d, 1e-6) is
+ * rounded to FP32; terms are accumulated in FP64 (FP32 pipe) or in Kahan-compensated
+ * FP32 per thread then FP64 (tensor-core kernel), in a fixed order per launch shape. */
 cc_status cc_interaction_sum(const cc_points *p, int64_t n, uint32_t r2,
                              float *d_sum, unsigned long long *d_count, void *stream);
 
@@ -132,8 +134,8 @@ cc_status cc_stream_status(void *stream);
  *   CC_MODE_RANGE_ERROR  span above 32767: nothing was counted
  *   CC_MODE_FP32_SPHERES FP32 spheres
  *   CC_MODE_TENSOR       integer points, the same exact form as a TF32 tensor-core
- *                        contraction (counts only, n >= 16384, and only while the
- *                        absolute values of its eight terms sum to less than 2^24)
+ *                        contraction (n >= 16384, and only while the absolute values
+ *                        of its eight terms sum to less than 2^24)
  * CC_ERR_NOT_FOUND when no call has run on `stream` yet. */
 enum {
     CC_MODE_FP32_EXACT = 0,
@@ -145,8 +147,9 @@ enum {
 cc_status cc_stream_mode(void *stream, int32_t *mode);
 
 /* Enables (1, the default) or disables (0) the tensor-core kernel for later
- * cc_count_pairs calls of this process; when disabled every integer count runs on the
- * FP32 pipe. Results are identical either way (both are exact); the switch exists to
+ * cc_count_pairs / cc_interaction_sum calls of this process; when disabled every integer
+ * set runs on the FP32 pipe. Counts are identical either way (both are exact; sums agree
+ * to the rounding of their accumulation order); the switch exists to
  * compare the two kernels and to keep the tensor cores free for other work. The initial
  * value comes from the environment variable CC_TC (0 disables). Always CC_OK. */
 cc_status cc_set_tensor_cores(int32_t enable);

@@ -38,8 +38,9 @@ cc_status plan_launch_sets(cc_plan *P, int32_t n_sets, int32_t want_sum, unsigne
                            float *d_sums, cudaStream_t s);
 size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc);
 bool tc_enabled();
-// Integer sets at least this large have their count queries served by the single-set
-// path (the tensor-core kernel when the set's range admits it) instead of the batch.
+// Integer sets at least this large have their count and sum queries served by the
+// single-set path (the tensor-core kernel when the set's range admits it) instead of the
+// batch.
 constexpr int64_t kServerTcMinN = 16384;
 void *plan_sets_buffer_v(cc_plan *P);
 size_t plan_set_desc_bytes();
@@ -70,7 +71,7 @@ struct SetRec {
     size_t bytes = 0;
     int32_t refs = 0;
     bool alive = false;
-    bool single = false;    // count queries go to the single-set (tensor-core) path
+    bool single = false;    // queries go to the single-set (tensor-core) path
 };
 
 struct Lane {
@@ -197,8 +198,8 @@ static bool launch(cc_server *S, Lane &L) {
             d.n = sr.n;
             d.dtype = sr.dtype;
             d.r2 = batch[k].r2;
-            if (sr.single && batch[k].op == CC_OP_COUNT) {
-                d.n = 0;   // the batch writes 0; the single-set call below writes the count
+            if (sr.single) {
+                d.n = 0;   // the batch writes 0; the single-set call below writes the result
                 singles.push_back(static_cast<int32_t>(k));
             }
             L.h_sets[k] = d;
@@ -213,7 +214,7 @@ static bool launch(cc_server *S, Lane &L) {
         cc_status st = e == cudaSuccess
                            ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
                            : CC_ERR_CUDA;
-        // large integer count queries: one single-set call each, stream-ordered after the
+        // queries on large integer sets: one single-set call each, stream-ordered after the
         // batch (this thread is the lane stream's only user, so its workspace is too)
         for (size_t j = 0; st == CC_OK && j < singles.size(); ++j) {
             const int32_t k = singles[j];
@@ -225,7 +226,9 @@ static bool launch(cc_server *S, Lane &L) {
             pts.y = static_cast<char *>(sr.buf) + col;
             pts.z = static_cast<char *>(sr.buf) + 2 * col;
             pts.r = nullptr;
-            st = cc_count_pairs(&pts, sr.n, L.batch[k].r2, L.d_counts + k, L.stream);
+            st = L.batch[k].op == CC_OP_SUM
+                     ? cc_interaction_sum(&pts, sr.n, L.batch[k].r2, L.d_sums + k, L.d_counts + k, L.stream)
+                     : cc_count_pairs(&pts, sr.n, L.batch[k].r2, L.d_counts + k, L.stream);
             S->single_launches += 1;
         }
         if (st == CC_OK) e = cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(unsigned long long) * nb,
@@ -322,7 +325,7 @@ cc_status cc_server_register_set(cc_server *S, const cc_points *p, int64_t n, in
         if (p->dtype == CC_I32 && n >= kServerTcMinN && tc_enabled()) {
             // both lanes may hold a workspace of this size (allocated by the scheduler on
             // first use); without room in the budget the set stays on the batched path
-            const size_t need = 2 * single_ws_bytes(n, false, true);
+            const size_t need = 2 * std::max(single_ws_bytes(n, false, true), single_ws_bytes(n, true, true));
             const size_t extra = need > S->single_ws_reserved ? need - S->single_ws_reserved : 0;
             if (S->resident_bytes + S->inflight_bytes + extra <= S->budget) {
                 S->resident_bytes += extra;

@@ -40,7 +40,7 @@ size_t tc_region_bytes(int64_t n);
 bool tc_enabled();
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream);
 cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
-                           cudaStream_t stream);
+                           float *d_sum, double *partial, cudaStream_t stream);
 // Smallest set for which counts take the tensor-core kernel.
 constexpr int64_t TC_MIN_N = 16384;
 
@@ -771,7 +771,8 @@ static cc_status pick_launch(int64_t n, bool f32, bool sum, Launch &L) {
 }
 
 static bool use_tc(int64_t n, bool sum, bool allow_tc) {
-    return allow_tc && !sum && n >= TC_MIN_N && tc_enabled();
+    (void)sum;   // counts and interaction sums alike
+    return allow_tc && n >= TC_MIN_N && tc_enabled();
 }
 
 // Workspace layout: WsHeader | region | double partial[grid], where the region holds
@@ -785,7 +786,8 @@ size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc) {
     size_t region = static_cast<size_t>(g.nrec) * sizeof(Rec);
     if (use_tc(n, sum, allow_tc)) region = std::max(region, tc_region_bytes(n));
     region = (region + 255) & ~static_cast<size_t>(255);
-    return sizeof(WsHeader) + region + static_cast<size_t>(g.grid) * sizeof(double) + 256;
+    const size_t slots = static_cast<size_t>(std::max<int64_t>(g.grid, sm_count()));   // CTAs of either kernel
+    return sizeof(WsHeader) + region + slots * sizeof(double) + 256;
 }
 
 // Enqueues the whole single-set path on `stream` using workspace `ws` (>= single_ws_bytes).
@@ -852,7 +854,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     // In tensor-core mode the device picks between the two kernels: each returns at once
     // unless the preparation kernel chose its mode.
     if (tc) {
-        st = tc_enqueue_pairs(n, region, hdr, d_count, stream);
+        st = tc_enqueue_pairs(n, region, hdr, d_count, d_sum, partial, stream);
         if (st != CC_OK) return st;
     }
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.threads), args, L.smem, stream));

@@ -146,6 +146,8 @@ struct TcArgs {
     int32_t h;              // (n-1)/2
     WsHeader *hdr;
     unsigned long long *d_count;
+    float *d_sum;           // interaction sum (sum kernels only)
+    double *partial;        // one FP64 slot per CTA (sum kernels only)
     uint64_t wait_ns;
     int32_t stall;          // test hook: the copy warp issues nothing
     int32_t pad;
@@ -161,7 +163,8 @@ struct TcSmem {
     static constexpr int kNBars = 5 + 2 * NS + 2 * NB;
     static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
-    static constexpr int kTotal = kRed + EPW * 8;
+    static constexpr int kRedSum = kRed + EPW * 8;        // per-epilogue-warp sums
+    static constexpr int kTotal = kRedSum + EPW * 8;
 };
 
 __device__ __forceinline__ f2 f2_fma_rm(f2 a, f2 b, f2 c) {
@@ -179,6 +182,23 @@ __device__ __forceinline__ uint32_t acc_count(f2 a) {
     return ((~lo) & 0x7FFFFFu) + ((~hi) & 0x7FFFFFu);
 }
 
+// One interaction term 1/max(d, 1e-6) from the exact d^2: square root and reciprocal each
+// correctly rounded in FP32 (the FP32-pipe kernels' term, before its widening to FP64).
+__device__ __forceinline__ float term_f32(float d2) {
+    return __frcp_rn(fmaxf(__fsqrt_rn(d2), 1e-6f));
+}
+
+// Kahan's compensated summation: the error stays within (2u + O(k u^2)) times the sum of the
+// k (positive) terms, u = 2^-24, so FP32 serves for the whole kernel (k u^2 < 1e-8 for the
+// largest per-thread term counts) and the FP64 pipe, slow on this part, is kept off the
+// per-hit path.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
 // JS objects per j-stage (MMA N), NB accumulators of JS TMEM columns (NB * JS = 512),
 // EPW epilogue warps, NS-deep j-stage ring. Of each epilogue thread's CPW values per
 // unit, SCR are screened on the integer ALU (a three-input OR of the raw bits per two
@@ -189,8 +209,14 @@ __device__ __forceinline__ uint32_t acc_count(f2 a) {
 // each j-stage slot and each i-tile slot (plain arrivals once it has seen the completion
 // of the MMAs that read them), leaving the MMA thread one commit per unit. The MMA
 // thread is the pipeline's critical path (it shares its SMSP with two counting warps);
-// both measured faster and are on in the default shape.
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false>
+// both measured faster and are on in the default shape. SUMT: the interaction sum as well.
+// Every value is screened with the ALU OR; where the warp holds a hit, the groups of 8
+// columns that hold one are re-read from TMEM and walked exactly before the accumulator is
+// handed back, counting and adding 1/max(d, 1e-6) with d^2 = v + r2e + 1 exact in FP32, in
+// a Kahan-compensated FP32 sum per thread. (Walking the register copy instead, with the
+// accumulator handed back at once, keeps all 128 values live through the walk: it spilled
+// and measured slower at every hit density.)
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -210,6 +236,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
+    double *red_sum = reinterpret_cast<double *>(smem + L::kRedSum);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -362,6 +389,9 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         const uint32_t lane_addr = static_cast<uint32_t>(quarter * 32) << 16;
         f2 acc[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
         unsigned long long cnt = 0;
+        double sum = 0.0;
+        float ks = 0.0f, kc = 0.0f;   // Kahan-compensated FP32 sum of the terms
+        const float off_f = static_cast<float>(A.hdr->ai_off);   // r2e + 1, exact in FP32
         int64_t t = t0;
         int32_t st = s0;
         int32_t buf = 0;
@@ -388,36 +418,102 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             tc_fence_after();
             uint32_t v[CPW];
             tmem_ld<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
-            // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
-            // before counting, so the next MMA overlaps this warp's arithmetic
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&t_empty[buf]);
+            if (!SUMT) {
+                // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
+                // before counting, so the next MMA overlaps this warp's arithmetic
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t_empty[buf]);
+            }
             const bool full = eo0 >= TC_T && eo0 + JS - 1 <= A.h;
-            if (full) {
-                constexpr int NF = CPW - SCR;   // values counted on the FP32 pipe
-                static_assert(SCR % 2 == 0 && NF % 8 == 0, "split of the values");
+            if (SUMT) {
+                // screen: any negative value (or -0) in the warp's block of the accumulator?
+                uint32_t orv = 0;
 #pragma unroll
-                for (int j = 0; j < NF / 2; ++j) {
-                    const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
-                    acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
-                }
-                if constexpr (SCR > 0) {
-                    uint32_t orv = 0;
+                for (int j = 0; j < CPW; j += 2) orv |= v[j] | v[j + 1];
+                if (__any_sync(0xFFFFFFFFu, orv & 0x80000000u)) {
+                    // one bit per group of 8 columns holding one, warp-uniform
+                    uint32_t gm = 0;
 #pragma unroll
-                    for (int j = NF; j < CPW; j += 2) orv |= v[j] | v[j + 1];
-                    if (orv & 0x80000000u) {   // a negative value (or -0) among them
+                    for (int g = 0; g < CPW / 8; ++g) {
+                        uint32_t o8 = 0;
 #pragma unroll
-                        for (int j = NF; j < CPW; ++j) cnt += __uint_as_float(v[j]) < 0.0f ? 1u : 0u;
+                        for (int j = 0; j < 8; ++j) o8 |= v[8 * g + j];
+                        gm |= (o8 >> 31) << g;
                     }
-                }
-            } else {
-                const int64_t i = t * TC_T + row;
-                const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
-                const int64_t d0 = static_cast<int64_t>(eo0) + part * CPW - row;   // e - i of column 0
+                    gm = __reduce_or_sync(0xFFFFFFFFu, gm);
+                    // walk the flagged groups exactly (compact code: one group at a time)
+                    // columns c of this row that the schedule assigns: 1 <= d0 + c <= ev
+                    int32_t clo = 0, cspan = CPW - 1;
+                    if (!full) {
+                        const int64_t i = t * TC_T + row;
+                        const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
+                        const int64_t d0 = static_cast<int64_t>(eo0) + part * CPW - row;   // e - i of column 0
+                        const int64_t lo = 1 - d0 > 0 ? 1 - d0 : 0;
+                        const int64_t hi = ev - d0 < CPW - 1 ? ev - d0 : CPW - 1;
+                        if (hi >= lo) {
+                            clo = static_cast<int32_t>(lo);
+                            cspan = static_cast<int32_t>(hi - lo);
+                        } else {   // none: c - clo is negative, above any span as unsigned
+                            clo = 1 << 30;
+                            cspan = 0;
+                        }
+                    }
+                    do {
+                        const int g = __ffs(gm) - 1;
+                        gm &= gm - 1;
+                        // re-read the group from TMEM (the buffer is still held): no dynamic
+                        // register indexing, and v is dead past the screen
+                        uint32_t w[8], m8 = 0;
+                        tmem_ld8(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW + 8 * g), w);
 #pragma unroll
-                for (int j = 0; j < CPW; ++j)
-                    cnt += (d0 + j >= 1 && d0 + j <= ev && __uint_as_float(v[j]) < 0.0f) ? 1u : 0u;
+                        for (int j = 0; j < 8; ++j) m8 |= __uint_as_float(w[j]) < 0.0f ? (1u << j) : 0u;
+                        uint32_t ok = 0;   // columns 8g+j inside the row's window
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            ok |= static_cast<uint32_t>(8 * g + j - clo) <= static_cast<uint32_t>(cspan) ? (1u << j) : 0u;
+                        m8 &= ok;
+                        while (m8) {
+                            const int j = __ffs(m8) - 1;
+                            m8 &= m8 - 1;
+                            uint32_t u = w[0];
+#pragma unroll
+                            for (int k = 1; k < 8; ++k) u = j == k ? w[k] : u;
+                            ++cnt;
+                            kahan_add(ks, kc, term_f32(__fadd_rn(__uint_as_float(u), off_f)));
+                        }
+                    } while (gm);
+                }
+                // the walk is done with the accumulator: hand the TMEM buffer back
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t_empty[buf]);
+            } else {
+                if (full) {
+                    constexpr int NF = CPW - SCR;   // values counted on the FP32 pipe
+                    static_assert(SCR % 2 == 0 && NF % 8 == 0, "split of the values");
+#pragma unroll
+                    for (int j = 0; j < NF / 2; ++j) {
+                        const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
+                        acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
+                    }
+                    if constexpr (SCR > 0) {
+                        uint32_t orv = 0;
+#pragma unroll
+                        for (int j = NF; j < CPW; j += 2) orv |= v[j] | v[j + 1];
+                        if (orv & 0x80000000u) {   // a negative value (or -0) among them
+#pragma unroll
+                            for (int j = NF; j < CPW; ++j) cnt += __uint_as_float(v[j]) < 0.0f ? 1u : 0u;
+                        }
+                    }
+                } else {
+                    const int64_t i = t * TC_T + row;
+                    const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
+                    const int64_t d0 = static_cast<int64_t>(eo0) + part * CPW - row;   // e - i of column 0
+#pragma unroll
+                    for (int j = 0; j < CPW; ++j)
+                        cnt += (d0 + j >= 1 && d0 + j <= ev && __uint_as_float(v[j]) < 0.0f) ? 1u : 0u;
+                }
             }
             if ((q & 1023) == 1023) {
 #pragma unroll
@@ -439,9 +535,16 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) cnt += acc_count(acc[a]);
+        if (SUMT) sum += static_cast<double>(ks) - static_cast<double>(kc);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
-        if (lane == 0) red[ew] = cnt;
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+            if (SUMT) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+        }
+        if (lane == 0) {
+            red[ew] = cnt;
+            if (SUMT) red_sum[ew] = sum;
+        }
     }
     __syncwarp();   // lanes 1-31 of the copy and MMA warps wait for their lane 0
     tc_fence_before();
@@ -454,6 +557,21 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         unsigned long long c = 0;
         for (int i = 0; i < EPW; ++i) c += red[i];
         if (c && A.d_count) atomicAdd(A.d_count, c);
+        if (SUMT) {
+            // per-CTA FP64 partials, summed in CTA order by the last CTA to finish
+            double sm = 0.0;
+            for (int i = 0; i < EPW; ++i) sm += red_sum[i];
+            A.partial[blockIdx.x] = sm;
+            __threadfence();
+            const unsigned ticket = atomicAdd(&A.hdr->ticket1, 1u);
+            if (ticket == gridDim.x - 1) {
+                __threadfence();
+                double tot = 0.0;
+                for (unsigned b = 0; b < gridDim.x; ++b) tot += *reinterpret_cast<volatile double *>(&A.partial[b]);
+                *A.d_sum = static_cast<float>(tot);
+                A.hdr->ticket1 = 0;
+            }
+        }
     }
 }
 
@@ -487,10 +605,10 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false>
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -513,7 +631,8 @@ static int tc_variant() {
     return v;
 }
 
-static cc_status tc_pick(TcLaunch &L) {
+static cc_status tc_pick(TcLaunch &L, bool sum) {
+    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true>(L);
     switch (tc_variant()) {
         case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
         case 2: return tc_launch_of<128, 4, 8, 16, 0, true, true>(L);
@@ -527,7 +646,7 @@ static cc_status tc_pick(TcLaunch &L) {
 // MODE_I32_TC for this call. `region` holds tc_region_bytes(n).
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream) {
     TcLaunch L;
-    cc_status st = tc_pick(L);
+    cc_status st = tc_pick(L, false);   // the sum kernel has the same stage width
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
     const int64_t rows = std::max<int64_t>(g.M * TC_T, g.elen);
@@ -541,9 +660,9 @@ cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHead
 
 // Enqueues the tensor-core kernel (returns at once unless the mode is MODE_I32_TC).
 cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
-                           cudaStream_t stream) {
+                           float *d_sum, double *partial, cudaStream_t stream) {
     TcLaunch L;
-    cc_status st = tc_pick(L);
+    cc_status st = tc_pick(L, d_sum != nullptr);
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
     TcArgs A;
@@ -555,6 +674,8 @@ cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsi
     A.h = static_cast<int32_t>((n - 1) / 2);
     A.hdr = hdr;
     A.d_count = d_count;
+    A.d_sum = d_sum;
+    A.partial = partial;
     A.wait_ns = wait_limit_ns();
     A.stall = debug_stall();
     A.pad = 0;

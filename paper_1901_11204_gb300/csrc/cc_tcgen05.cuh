@@ -78,6 +78,16 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
 // Loads 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: thread t of
 // the warp reads lane base+t) and waits for them, in one statement so that no use of the
 // registers can be scheduled before the wait.
+// 8 consecutive 32-bit columns of this warp's 32 lanes (one register per column per lane).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "

@@ -1,4 +1,5 @@
-"""Tensor-core pair kernel (integer points, counts) against the CPU oracle, through the C ABI.
+"""Tensor-core pair kernel (integer points: counts and interaction sums) against the CPU
+oracle and the FP64 definition, through the C ABI.
 
 The device takes the TF32 tensor-core form only while the absolute values of its eight
 terms sum to less than 2^24 (then every partial sum is an exact FP32 integer). These
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.sum_ref import pair_sum_ref
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -150,18 +152,65 @@ def test_ragged_sizes(cc, n):
     assert got == oracle.count_i32(x, y, z, 400)
 
 
-def test_below_threshold_and_sums_use_fp32_pipe(cc):
+def test_below_threshold_uses_fp32_pipe(cc):
     rng = np.random.default_rng(3)
     x, y, z = box_points(rng, TC_MIN_N - 1, 1023)
     got, mode = gpu_count(cc, x, y, z, 400)
     assert mode == cc.MODE_FP32_EXACT
     assert got == oracle.count_i32(x, y, z, 400)
-    x, y, z = box_points(rng, TC_MIN_N + 5, 1023)
+
+
+SUM_RTOL = 1e-5
+
+
+def gpu_sum(cc, x, y, z, r2):
     t = dev(x, y, z)
-    s, c = cc.interaction_sum(*t, r2=400)
+    s, c = cc.interaction_sum(*t, r2=r2)
     torch.cuda.synchronize()
-    assert cc.stream_mode() == cc.MODE_FP32_EXACT
-    assert cc.as_u64(c) == oracle.count_i32(x, y, z, 400)
+    return float(s.item()), cc.as_u64(c), cc.stream_mode()
+
+
+@pytest.mark.parametrize("n,r2", [(TC_MIN_N, 4), (TC_MIN_N + 5, 400), (20001, 2000)])
+def test_sums_on_tensor_cores(cc, n, r2):
+    """Interaction sums take the tensor-core kernel too: count bit-exact, sum within
+    1e-5 of the FP64 definition and of the FP32-pipe kernel's sum."""
+    rng = np.random.default_rng(n + r2)
+    x, y, z = box_points(rng, n, 160)
+    s, c, mode = gpu_sum(cc, x, y, z, r2)
+    assert mode == cc.MODE_TENSOR
+    want_s, want_c = pair_sum_ref(x, y, z, r2)
+    assert c == want_c == oracle.count_i32(x, y, z, r2)
+    assert abs(s - want_s) <= SUM_RTOL * want_s
+    cc.set_tensor_cores(False)
+    try:
+        s2, c2, mode2 = gpu_sum(cc, x, y, z, r2)
+    finally:
+        cc.set_tensor_cores(True)
+    assert mode2 == cc.MODE_FP32_EXACT and c2 == c
+    assert abs(s - s2) <= SUM_RTOL * want_s
+
+
+def test_sums_near_ties_at_the_range_limit(cc):
+    rng = np.random.default_rng(150)
+    x, y, z = corner_near_ties(rng, 24001, 2046, 50)
+    x[0], y[0], z[0] = 0, 0, 0
+    x[1], y[1], z[1] = 2046, 2046, 2046
+    s, c, mode = gpu_sum(cc, x, y, z, 50)
+    assert mode == cc.MODE_TENSOR
+    want_s, want_c = pair_sum_ref(x, y, z, 50)
+    assert c == want_c
+    assert abs(s - want_s) <= SUM_RTOL * want_s
+
+
+def test_sums_all_points_identical(cc):
+    """Every pair hits at d = 0: each term is 1/1e-6."""
+    n = 20001
+    x = np.full(n, 17, np.int32)
+    s, c, mode = gpu_sum(cc, x, x.copy(), x.copy(), 0)
+    assert mode == cc.MODE_TENSOR
+    assert c == n * (n - 1) // 2
+    want = c / 1e-6
+    assert abs(s - want) <= SUM_RTOL * want
 
 
 def test_tc_bounded_wait_timeout(cc):
