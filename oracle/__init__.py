@@ -56,6 +56,8 @@ def _bind(path: str):
     lib.oracle_count_i32.restype = ctypes.c_uint64
     lib.oracle_count_i32_cyclic.argtypes = [i32p, i32p, i32p, ctypes.c_int64, ctypes.c_uint32]
     lib.oracle_count_i32_cyclic.restype = ctypes.c_uint64
+    lib.oracle_sum_i32.argtypes = [i32p, i32p, i32p, ctypes.c_int64, ctypes.c_uint32, f64p]
+    lib.oracle_sum_i32.restype = ctypes.c_uint64
     lib.oracle_count_f32.argtypes = [f32p, f32p, f32p, f32p, ctypes.c_int64, f64p]
     lib.oracle_count_f32.restype = ctypes.c_uint64
     lib.oracle_count_i32_sets.argtypes = [i32p, i32p, i32p, i64p, ctypes.c_int64,
@@ -120,6 +122,15 @@ def count_i32(x, y, z, r2: int) -> int:
     assert len(y) == n and len(z) == n
     return int(_load().oracle_count_i32(_p(x, ctypes.c_int32), _p(y, ctypes.c_int32),
                                         _p(z, ctypes.c_int32), n, int(r2)))
+
+
+def sum_i32(x, y, z, r2: int) -> tuple[int, float]:
+    """Standard algorithm over integer points: (count, FP64 sum of 1/max(d,1e-6))."""
+    x, y, z = _i32(x), _i32(y), _i32(z)
+    s = ctypes.c_double(0.0)
+    c = _load().oracle_sum_i32(_p(x, ctypes.c_int32), _p(y, ctypes.c_int32),
+                               _p(z, ctypes.c_int32), len(x), int(r2), ctypes.byref(s))
+    return int(c), float(s.value)
 
 
 def count_i32_cyclic(x, y, z, r2: int) -> int:

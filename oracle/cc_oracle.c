@@ -15,7 +15,7 @@
  * operation, in the order written (a pin in the tests fails if a build contracts).
  *
  * What each function follows:
- *   oracle_count_i32 / oracle_count_f32 -- the standard algorithm for symmetric
+ *   oracle_count_i32 / oracle_sum_i32 / oracle_count_f32 -- the standard algorithm for symmetric
  *       pairwise interactions (Section 4, "Standard algorithm for calculating SPI"):
  *       for every i, accumulate interact(obj[i], obj[j]) over every later j.
  *       The loop over i may be split across OpenMP threads; counts are integers, so
@@ -35,7 +35,8 @@
  *     Section 3). FP32 spheres collide when (dx*dx + dy*dy) + dz*dz <= (ri+rj)*(ri+rj),
  *     every operation rounded to nearest in FP32 in exactly that order.
  *   - The interaction sum adds 1/max(d, 1e-6) over the colliding pairs, with d the
- *     Euclidean distance computed in FP64 from the FP32 coordinates.
+ *     Euclidean distance computed in FP64 from the FP32 coordinates (spheres) or the
+ *     FP64 square root of the exact integer squared distance (integer points).
  *   - Counts are unsigned 64-bit (the paper's int counters would overflow).
  *   - Integer squared distances are formed in int64, so no input range limit applies.
  *   - NaN coordinates or radii make the FP32 comparison false.
@@ -111,6 +112,36 @@ uint64_t oracle_count_i32(const int32_t *x, const int32_t *y, const int32_t *z,
             c += (uint64_t)collide_i32(x[i], y[i], z[i], x[j], y[j], z[j], r2);
         count += c;
     }
+    return count;
+}
+
+/* Integer points: returns the count; *sum_out receives the FP64 interaction sum, each
+ * colliding pair adding 1 / max(d, 1e-6) with d = sqrt of the exact integer d2. */
+uint64_t oracle_sum_i32(const int32_t *x, const int32_t *y, const int32_t *z,
+                        int64_t n, uint32_t r2, double *sum_out) {
+    uint64_t count = 0;
+    double sum = 0.0;
+    int nt = oracle_get_threads();
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : count, sum) num_threads(nt)
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t c = 0;
+        double s = 0.0;
+        for (int64_t j = i + 1; j < n; ++j) {
+            int64_t dx = (int64_t)x[i] - (int64_t)x[j];
+            int64_t dy = (int64_t)y[i] - (int64_t)y[j];
+            int64_t dz = (int64_t)z[i] - (int64_t)z[j];
+            int64_t d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 <= (int64_t)r2) {
+                double d = sqrt((double)d2);
+                c += 1;
+                s += 1.0 / (d > 1e-6 ? d : 1e-6);
+            }
+        }
+        count += c;
+        sum += s;
+    }
+    if (sum_out) *sum_out = sum;
     return count;
 }
 

@@ -403,6 +403,49 @@ def pin_f32_sum_bruteforce(o):
         assert abs(s - want) <= 1e-12 * max(1.0, abs(want)), (s, want)
 
 
+def pin_i32_sum_lattice(o):
+    """All sites of a non-cubic box: each offset d (0 < |d|^2 <= r2) occurs
+    prod_a (L_a - |d_a|) times as an ordered pair, so the count is half the sum of those
+    multiplicities and the sum half the sum of multiplicity / |d|."""
+    rng = np.random.default_rng(13)
+    for L in [(5, 3, 4), (2, 7, 3)]:
+        x, y, z = lattice_points(L, rng)
+        for r2 in [1, 2, 5, 9]:
+            m = math.isqrt(r2)
+            cnt, terms = 0, []
+            for d in itertools.product(range(-m, m + 1), repeat=3):
+                d2 = sum(v * v for v in d)
+                if d2 == 0 or d2 > r2:
+                    continue
+                mult = math.prod(max(L[a] - abs(d[a]), 0) for a in range(3))
+                cnt += mult
+                terms.append(mult / math.sqrt(d2))
+            c, s = o.sum_i32(x, y, z, r2)
+            assert c == cnt // 2 == o.count_i32(x, y, z, r2), (L, r2)
+            want = math.fsum(terms) / 2
+            assert abs(s - want) <= 1e-12 * want, (L, r2, s, want)
+
+
+def pin_i32_sum_bruteforce(o):
+    """Random small integer sets (with coincident points: each such pair adds 1e6)
+    against all ordered pairs and math.fsum of the terms, halved."""
+    rng = np.random.default_rng(14)
+    for trial in range(8):
+        n = int(rng.integers(2, 50))
+        box = int(rng.choice([2, 3, 6]))
+        x, y, z = (rng.integers(0, box, n).astype(np.int32) for _ in range(3))
+        r2 = int(rng.integers(0, 3 * box * box))
+        terms = []
+        for i, j in itertools.permutations(range(n), 2):
+            d2 = int(x[i] - x[j]) ** 2 + int(y[i] - y[j]) ** 2 + int(z[i] - z[j]) ** 2
+            if d2 <= r2:
+                terms.append(1.0 / max(math.sqrt(d2), 1e-6))
+        c, s = o.sum_i32(x, y, z, r2)
+        assert c == len(terms) // 2, (trial, c, len(terms))
+        want = math.fsum(terms) / 2
+        assert abs(s - want) <= 1e-12 * max(1.0, want), (trial, s, want)
+
+
 ALL_PINS = [
     pin_fig1_worked_example,
     pin_cyclic_covers_every_pair_once,
@@ -422,4 +465,6 @@ ALL_PINS = [
     pin_f32_rounding_near_ties,
     pin_f32_symmetry,
     pin_f32_sum_bruteforce,
+    pin_i32_sum_lattice,
+    pin_i32_sum_bruteforce,
 ]

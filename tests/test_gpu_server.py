@@ -5,7 +5,6 @@ import pytest
 
 import oracle
 import synth
-from tests.sum_ref import pair_sum_ref
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -133,7 +132,7 @@ def test_cfg5_pool_sample(cc):
 def test_large_integer_sets_in_the_mix(cc):
     """Integer sets of n >= 16384: their count and sum queries run the single-set
     (tensor-core) path stream-ordered after the batch; every count equals the oracle and
-    every sum the FP64 definition, alone and mixed with small sets and FP32 spheres."""
+    every sum the oracle's FP64 sum, alone and mixed with small sets and FP32 spheres."""
     rng = np.random.default_rng(21)
     sets = []
     for n, box in ((20000, 200), (30001, 1024), (16384, 64)):
@@ -155,7 +154,7 @@ def test_large_integer_sets_in_the_mix(cc):
         assert res[rid]["status"] == 0 and res[rid]["count"] == want_c, (k, op)
         assert res2[rid + 10000]["count"] == want_c
         if op == cc.CC_OP_SUM:
-            want_s, c2 = pair_sum_ref(*sets[k][1:4], 9)
+            c2, want_s = oracle.sum_i32(*sets[k][1:4], 9)
             assert c2 == want_c
             for r in (res[rid], res2[rid + 10000]):
                 assert abs(r["sum"] - want_s) <= 1e-5 * want_s, (k, r["sum"], want_s)

@@ -165,15 +165,9 @@ def test_int_sum_parity(cc):
     n = 5000
     x, y, z = (rng.integers(0, 30, n).astype(np.int32) for _ in range(3))
     s, c = gpu_sum(cc, x, y, z, 4)
-    assert c == oracle.count_i32(x, y, z, 4)
-    # reference: the same pairs with d from the exact integer squared distance, in FP64
-    P = np.stack([x, y, z], 1).astype(np.int64)
-    tot = 0.0
-    for i in range(n):
-        d2 = ((P[i + 1:] - P[i]) ** 2).sum(1)
-        hit = d2[d2 <= 4]
-        tot += float((1.0 / np.maximum(np.sqrt(hit.astype(np.float64)), 1e-6)).sum())
-    assert rel(s, tot) <= SUM_RTOL
+    want_c, want_s = oracle.sum_i32(x, y, z, 4)
+    assert c == want_c == oracle.count_i32(x, y, z, 4)
+    assert rel(s, want_s) <= SUM_RTOL
 
 
 def test_stream_and_repeat_determinism(cc):

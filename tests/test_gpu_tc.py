@@ -1,5 +1,5 @@
 """Tensor-core pair kernel (integer points: counts and interaction sums) against the CPU
-oracle and the FP64 definition, through the C ABI.
+oracle (counts bit-exact, FP64 sums within 1e-5), through the C ABI.
 
 The device takes the TF32 tensor-core form only while the absolute values of its eight
 terms sum to less than 2^24 (then every partial sum is an exact FP32 integer). These
@@ -14,7 +14,6 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.sum_ref import pair_sum_ref
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -173,12 +172,12 @@ def gpu_sum(cc, x, y, z, r2):
 @pytest.mark.parametrize("n,r2", [(TC_MIN_N, 4), (TC_MIN_N + 5, 400), (20001, 2000)])
 def test_sums_on_tensor_cores(cc, n, r2):
     """Interaction sums take the tensor-core kernel too: count bit-exact, sum within
-    1e-5 of the FP64 definition and of the FP32-pipe kernel's sum."""
+    1e-5 of the oracle's FP64 sum and of the FP32-pipe kernel's sum."""
     rng = np.random.default_rng(n + r2)
     x, y, z = box_points(rng, n, 160)
     s, c, mode = gpu_sum(cc, x, y, z, r2)
     assert mode == cc.MODE_TENSOR
-    want_s, want_c = pair_sum_ref(x, y, z, r2)
+    want_c, want_s = oracle.sum_i32(x, y, z, r2)
     assert c == want_c == oracle.count_i32(x, y, z, r2)
     assert abs(s - want_s) <= SUM_RTOL * want_s
     cc.set_tensor_cores(False)
@@ -197,7 +196,7 @@ def test_sums_near_ties_at_the_range_limit(cc):
     x[1], y[1], z[1] = 2046, 2046, 2046
     s, c, mode = gpu_sum(cc, x, y, z, 50)
     assert mode == cc.MODE_TENSOR
-    want_s, want_c = pair_sum_ref(x, y, z, 50)
+    want_c, want_s = oracle.sum_i32(x, y, z, 50)
     assert c == want_c
     assert abs(s - want_s) <= SUM_RTOL * want_s
 

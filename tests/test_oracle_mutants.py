@@ -57,6 +57,11 @@ MUTANTS = {
     "alg2_no_halving": ("return contacts / 2;", "return contacts;"),
     "sets_all_ordered": ("for (int64_t j = i + 1; j < b; ++j)\n                c += (uint64_t)collide_i32",
                          "for (int64_t j = a; j < b; ++j)\n                c += (uint64_t)collide_i32"),
+    "i32_sum_no_floor": ("s += 1.0 / (d > 1e-6 ? d : 1e-6);", "s += 1.0 / d;"),
+    "i32_sum_d2_not_d": ("double d = sqrt((double)d2);", "double d = (double)d2;"),
+    "i32_sum_strict": ("if (d2 <= (int64_t)r2) {\n                double d", "if (d2 < (int64_t)r2) {\n                double d"),
+    "i32_sum_dropped_dy": ("int64_t d2 = dx * dx + dy * dy + dz * dz;\n            if (d2 <= (int64_t)r2) {\n                double d",
+                           "int64_t d2 = dx * dx + dz * dz;\n            if (d2 <= (int64_t)r2) {\n                double d"),
     "work_formula": ("return (n - 1) / 2 + ((n % 2 == 0 && i < n / 2) ? 1 : 0);",
                      "return n / 2;"),
 }
