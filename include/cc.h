@@ -136,13 +136,19 @@ cc_status cc_stream_status(void *stream);
  *   CC_MODE_TENSOR       integer points, the same exact form as a TF32 tensor-core
  *                        contraction (n >= 16384, and only while the absolute values
  *                        of its eight terms sum to less than 2^24)
+ *   CC_MODE_TENSOR_SPHERES FP32 spheres, n >= 16384: an exact integer screen of
+ *                        quantised coordinates on the tensor cores passes every pair
+ *                        that can collide, and the FP32 predicate above decides each
+ *                        screened pair (all coordinates and radii finite, and the
+ *                        largest 2|r| at most 2.2 % of the largest coordinate span)
  * CC_ERR_NOT_FOUND when no call has run on `stream` yet. */
 enum {
     CC_MODE_FP32_EXACT = 0,
     CC_MODE_INT_WIDE = 1,
     CC_MODE_RANGE_ERROR = 2,
     CC_MODE_FP32_SPHERES = 3,
-    CC_MODE_TENSOR = 4
+    CC_MODE_TENSOR = 4,
+    CC_MODE_TENSOR_SPHERES = 5
 };
 cc_status cc_stream_mode(void *stream, int32_t *mode);
 

@@ -245,6 +245,7 @@ def stream_status(stream=None) -> int:
 # Pair kernel chosen by the device for the last single-set call on a stream
 # (cc_stream_mode): the CC_MODE_* values of cc.h.
 MODE_FP32_EXACT, MODE_INT_WIDE, MODE_RANGE_ERROR, MODE_FP32_SPHERES, MODE_TENSOR = 0, 1, 2, 3, 4
+MODE_TENSOR_SPHERES = 5
 
 
 def set_tensor_cores(enable: bool) -> None:

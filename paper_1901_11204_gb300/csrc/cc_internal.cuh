@@ -47,7 +47,9 @@ enum : int32_t {
     MODE_I32_WIDE = 1,   // int32 difference form (spans up to 32767)
     MODE_RANGE_ERR = 2,  // span above 32767: nothing is counted
     MODE_F32 = 3,        // FP32 spheres
-    MODE_I32_TC = 4      // fast exact form as a TF32 tensor-core contraction (count only)
+    MODE_I32_TC = 4,     // fast exact form as a TF32 tensor-core contraction
+    MODE_F32_TC = 5      // FP32 spheres: exact integer screen on the tensor cores, then the
+                         // FP32 predicate for the screened pairs
 };
 
 // Workspace header: lives at the start of each stream's scratch buffer.
@@ -61,12 +63,16 @@ struct WsHeader {
     uint32_t ticket0;     // last-block ticket of the min/max reduction
     uint32_t ticket1;     // last-block ticket of the sum reduction
     uint32_t status;      // ST_* bits since the last cc_stream_status()
-    uint32_t pad[17];
+    float qmin[3];        // FP32 spheres, tensor-core screen: per-axis minimum coordinate
+    uint32_t qbad;        // ... non-zero when a coordinate or radius is not finite
+    uint32_t qrmax;       // ... largest |radius| (bits of a non-negative float)
+    double qscale;        // ... quantisation scale, 2046 / the largest per-axis span
+    uint32_t pad[10];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 static_assert(int{MODE_I32_FAST} == int{CC_MODE_FP32_EXACT} && int{MODE_I32_WIDE} == int{CC_MODE_INT_WIDE} &&
                   int{MODE_RANGE_ERR} == int{CC_MODE_RANGE_ERROR} && int{MODE_F32} == int{CC_MODE_FP32_SPHERES} &&
-                  int{MODE_I32_TC} == int{CC_MODE_TENSOR},
+                  int{MODE_I32_TC} == int{CC_MODE_TENSOR} && int{MODE_F32_TC} == int{CC_MODE_TENSOR_SPHERES},
               "device modes are the public CC_MODE_* values");
 
 // Largest half-span m = ceil(span/2) for which the FP32 expanded-square form is exact:
@@ -239,6 +245,14 @@ __device__ __forceinline__ float f2_hi(f2 v) {
 // Order-preserving unsigned encoding of int32 (for atomicMin/atomicMax on u32).
 __device__ __forceinline__ uint32_t ord_enc(int32_t v) { return static_cast<uint32_t>(v) ^ 0x80000000u; }
 __device__ __forceinline__ int32_t ord_dec(uint32_t u) { return static_cast<int32_t>(u ^ 0x80000000u); }
+// Order-preserving encoding of a finite float (larger float, larger code) and its inverse.
+__device__ __forceinline__ uint32_t ord_enc_f(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord_dec_f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
 
 #endif  // __CUDACC__
 

@@ -39,8 +39,8 @@ namespace cc {
 size_t tc_region_bytes(int64_t n);
 bool tc_enabled();
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream);
-cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
-                           float *d_sum, double *partial, cudaStream_t stream);
+cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region, WsHeader *hdr,
+                           unsigned long long *d_count, float *d_sum, double *partial, cudaStream_t stream);
 // Smallest set for which counts take the tensor-core kernel.
 constexpr int64_t TC_MIN_N = 16384;
 
@@ -59,6 +59,8 @@ __global__ void k_reset(WsHeader *h, int32_t mode, unsigned long long *d_count, 
         h->cx = h->cy = h->cz = 0;
         h->ticket0 = 0;
         h->ticket1 = 0;
+        h->qbad = 0u;
+        h->qrmax = 0u;
         if (d_count) *d_count = 0ull;
         if (d_sum) *d_sum = 0.0f;
     }
@@ -133,6 +135,95 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
     h->ticket0 = 0;
 }
 
+// FP32 spheres, tensor-core screen: per-axis min/max of the coordinates, the largest
+// |radius| and whether any value is not finite; the last block decides between the
+// screened tensor-core form (MODE_F32_TC) and the FP32-pipe kernel (MODE_F32).
+//
+// Screen: coordinates are quantised as X = floor((x - min) * S), S = 2046 / the largest
+// per-axis span, so |(X_i - X_j) - (x_i - x_j) S| < 1 per axis and the integer distance
+// D of a pair is below d S + sqrt(3). A pair the FP32 predicate accepts has
+// d <= |r_i + r_j| (1 + 2.5e-7) (five roundings in d^2, three in (r_i + r_j)^2), or d so
+// small that d^2 underflows (then D <= sqrt(3)). So every such pair has
+// D^2 <= r2q = ceil((2 rmax S (1 + 1e-6) + 1.7331)^2), and the tensor-core kernel counts
+// the integer form D^2 <= r2q exactly (the same 8-term contraction as integer points,
+// coordinates within [0, 2046]) and applies the FP32 predicate to those pairs only.
+// Admitted while r2q <= 2048 (2 rmax at most about 2.2 % of the span), so that screened
+// pairs stay rare for spread-out sets.
+constexpr int64_t F32_TC_MAX_R2Q = 2048;
+
+__global__ void k_minmax_f32(const float *__restrict__ x, const float *__restrict__ y,
+                             const float *__restrict__ z, const float *__restrict__ r, int64_t n, WsHeader *h,
+                             int32_t allow_tc) {
+    uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    uint32_t mx[3] = {0u, 0u, 0u};
+    uint32_t rmax = 0u, bad = 0u;
+    const float *c[3] = {x, y, z};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float v = c[a][i];
+            bad |= isfinite(v) ? 0u : 1u;
+            const uint32_t u = ord_enc_f(v);
+            mn[a] = min(mn[a], u);
+            mx[a] = max(mx[a], u);
+        }
+        const float rv = r[i];
+        bad |= isfinite(rv) ? 0u : 1u;
+        rmax = max(rmax, __float_as_uint(fabsf(rv)));   // non-negative floats order as their bits
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = __reduce_min_sync(0xFFFFFFFFu, mn[a]);
+        mx[a] = __reduce_max_sync(0xFFFFFFFFu, mx[a]);
+    }
+    rmax = __reduce_max_sync(0xFFFFFFFFu, rmax);
+    bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&h->umin[a], mn[a]);
+            atomicMax(&h->umax[a], mx[a]);
+        }
+        atomicMax(&h->qrmax, rmax);
+        if (bad) atomicOr(&h->qbad, 1u);
+    }
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&h->ticket0, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    int32_t mode = MODE_F32;
+    if (allow_tc && atomicAdd(&h->qbad, 0u) == 0u) {
+        double span = 0.0;
+        float lo[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = ord_dec_f(atomicAdd(&h->umin[a], 0u));
+            const float hi = ord_dec_f(atomicAdd(&h->umax[a], 0u));
+            span = fmax(span, static_cast<double>(hi) - static_cast<double>(lo[a]));
+        }
+        const double S = span > 0.0 ? 2046.0 / span : 1.0;
+        const double rm = static_cast<double>(__uint_as_float(atomicAdd(&h->qrmax, 0u)));
+        const double reach = 2.0 * rm * S * (1.0 + 1e-6) + 1.7331;
+        if (reach < 64.0 && isfinite(S)) {
+            const int64_t r2q = static_cast<int64_t>(ceil(reach * reach));
+            if (r2q <= F32_TC_MAX_R2Q && tc_exact(1023, r2q)) {
+                mode = MODE_F32_TC;
+                for (int a = 0; a < 3; ++a) h->qmin[a] = lo[a];
+                h->qscale = S;
+                h->cx = h->cy = h->cz = 1023;
+                h->r2e = static_cast<uint32_t>(r2q);
+                h->ai_off = static_cast<int32_t>(r2q + 1);
+            }
+        }
+    }
+    h->mode = mode;
+    h->ticket0 = 0;
+}
+
 // Fills the extended pair-interleaved array from integer SoA input.
 __global__ void k_fill_i32(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
                            const int32_t *__restrict__ z, int64_t n, int64_t nrec,
@@ -167,7 +258,8 @@ __global__ void k_fill_i32(const int32_t *__restrict__ x, const int32_t *__restr
 // Fills the extended pair-interleaved array from FP32 sphere SoA input.
 __global__ void k_fill_f32(const float *__restrict__ x, const float *__restrict__ y,
                            const float *__restrict__ z, const float *__restrict__ r, int64_t n,
-                           int64_t nrec, Rec *__restrict__ E) {
+                           int64_t nrec, Rec *__restrict__ E, const WsHeader *__restrict__ h) {
+    if (h->mode == MODE_F32_TC) return;   // the tensor-core kernel has its own operands
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrec;
          q += (int64_t)gridDim.x * blockDim.x) {
         Rec rec;
@@ -313,8 +405,10 @@ __global__ void __launch_bounds__(NT + 32, MINB) k_pairs(PairArgs A) {
 
     const int tid = threadIdx.x;
     const int warp = tid / 32;
-    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
-    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC) return;   // invalid, or the tensor-core kernel runs
+    const int32_t hmode = A.hdr->mode;
+    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : hmode;
+    // invalid, or one of the tensor-core forms runs this call
+    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC || hmode == MODE_F32_TC) return;
 
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) {
@@ -503,8 +597,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_pairs_w(PairArgs A) {
     unsigned long long *red_cnt = reinterpret_cast<unsigned long long *>(smem + L::kStages + L::kBars);
     double *red_sum = reinterpret_cast<double *>(red_cnt + (NW + 1));
 
-    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : A.hdr->mode;
-    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC) return;   // invalid, or the tensor-core kernel runs
+    const int32_t hmode = A.hdr->mode;
+    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : hmode;
+    // invalid, or one of the tensor-core forms runs this call
+    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC || hmode == MODE_F32_TC) return;
 
     if (lane == 0) {
         for (int i = 0; i < NS; ++i) mbar_init(&full[i], 1);
@@ -803,7 +899,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     cc_status st = pick_launch(n, f32, sum, L);
     if (st != CC_OK) return st;
     Geometry g = geometry(n, L);
-    const bool tc = !f32 && use_tc(n, sum, allow_tc);
+    const bool tc = use_tc(n, sum, allow_tc);
     uint8_t *region = reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader);
     size_t region_bytes = static_cast<size_t>(g.nrec) * sizeof(Rec);
     if (tc) region_bytes = std::max(region_bytes, tc_region_bytes(n));
@@ -829,9 +925,21 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
             if (st != CC_OK) return st;
         }
     } else {
+        if (tc) {
+            const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+            k_minmax_f32<<<mm_blocks, 256, 0, stream>>>(static_cast<const float *>(p->x),
+                                                         static_cast<const float *>(p->y),
+                                                         static_cast<const float *>(p->z), p->r, n, hdr, 1);
+            CC_CUDA(cudaGetLastError());
+        }
         k_fill_f32<<<prep_blocks, prep_threads, 0, stream>>>(
             static_cast<const float *>(p->x), static_cast<const float *>(p->y),
-            static_cast<const float *>(p->z), p->r, n, g.nrec, E);
+            static_cast<const float *>(p->z), p->r, n, g.nrec, E, hdr);
+        CC_CUDA(cudaGetLastError());
+        if (tc) {
+            st = tc_enqueue_fill(p, n, region, hdr, stream);
+            if (st != CC_OK) return st;
+        }
     }
     CC_CUDA(cudaGetLastError());
     PairArgs A;
@@ -852,9 +960,10 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     const bool prof = profiling();
     if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
     // In tensor-core mode the device picks between the two kernels: each returns at once
-    // unless the preparation kernel chose its mode.
+    // unless the preparation kernel chose its mode (integer points: MODE_I32_TC or an
+    // FP32-pipe mode; spheres: MODE_F32_TC or MODE_F32).
     if (tc) {
-        st = tc_enqueue_pairs(n, region, hdr, d_count, d_sum, partial, stream);
+        st = tc_enqueue_pairs(p, n, region, hdr, d_count, d_sum, partial, stream);
         if (st != CC_OK) return st;
     }
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.threads), args, L.smem, stream));
@@ -892,7 +1001,7 @@ cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned 
                                                static_cast<const int32_t *>(p->z), n, nrec, E, hdr);
     } else {
         k_fill_f32<<<blocks, 256, 0, stream>>>(static_cast<const float *>(p->x), static_cast<const float *>(p->y),
-                                               static_cast<const float *>(p->z), p->r, n, nrec, E);
+                                               static_cast<const float *>(p->z), p->r, n, nrec, E, hdr);
     }
     CC_CUDA(cudaGetLastError());
     using L = WarpSmem<NW, JS, NS>;

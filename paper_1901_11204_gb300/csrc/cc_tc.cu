@@ -85,13 +85,26 @@ size_t tc_region_bytes(int64_t n) {
 }
 
 // ---------------------------------------------------------------------------------------
-// operand fill (runs only when the device chose MODE_I32_TC)
+// operand fill (runs only when the device chose MODE_I32_TC or MODE_F32_TC)
 // ---------------------------------------------------------------------------------------
 
-__global__ void k_fill_tc(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
-                          const int32_t *__restrict__ z, int64_t n, int64_t arows, int64_t elen,
-                          uint8_t *__restrict__ Aop, uint8_t *__restrict__ Bop, const WsHeader *__restrict__ h) {
-    if (h->mode != MODE_I32_TC) return;
+// Integer coordinate of object p on one axis, before centring: the caller's integer, or
+// for FP32 spheres the quantised floor((v - min) * S) in [0, 2046] (computed in FP64).
+template <bool F32>
+__device__ __forceinline__ int32_t tc_coord(const void *c, int64_t p, int axis, const WsHeader *h) {
+    if constexpr (F32) {
+        const double v = static_cast<double>(static_cast<const float *>(c)[p]);
+        return static_cast<int32_t>(floor((v - static_cast<double>(h->qmin[axis])) * h->qscale));
+    } else {
+        return static_cast<const int32_t *>(c)[p];
+    }
+}
+
+template <bool F32>
+__global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y, const void *__restrict__ z,
+                          int64_t n, int64_t arows, int64_t elen, uint8_t *__restrict__ Aop,
+                          uint8_t *__restrict__ Bop, const WsHeader *__restrict__ h) {
+    if (h->mode != (F32 ? MODE_F32_TC : MODE_I32_TC)) return;
     const int32_t cx = h->cx, cy = h->cy, cz = h->cz;
     const int32_t off = h->ai_off;   // r2e + 1
     const int64_t rows = arows > elen ? arows : elen;
@@ -102,7 +115,8 @@ __global__ void k_fill_tc(const int32_t *__restrict__ x, const int32_t *__restri
         if (r < arows) {
             float4 lo, hi;
             if (r < n) {
-                const int32_t xi = x[r] - cx, yi = y[r] - cy, zi = z[r] - cz;
+                const int32_t xi = tc_coord<F32>(x, r, 0, h) - cx, yi = tc_coord<F32>(y, r, 1, h) - cy,
+                              zi = tc_coord<F32>(z, r, 2, h) - cz;
                 const int32_t c = xi * xi + yi * yi + zi * zi - off;
                 const int32_t cC = ((c + 1024) & 2047) - 1024;
                 const int32_t c1 = (c - cC) >> 11;   // exact: c - cC is a multiple of 2^11
@@ -122,7 +136,8 @@ __global__ void k_fill_tc(const int32_t *__restrict__ x, const int32_t *__restri
         }
         if (r < elen) {
             const int64_t p = r < n ? r : r % n;
-            const int32_t xj = x[p] - cx, yj = y[p] - cy, zj = z[p] - cz;
+            const int32_t xj = tc_coord<F32>(x, p, 0, h) - cx, yj = tc_coord<F32>(y, p, 1, h) - cy,
+                          zj = tc_coord<F32>(z, p, 2, h) - cz;
             const int32_t nj = xj * xj + yj * yj + zj * zj;
             const float4 lo = make_float4(static_cast<float>(xj), static_cast<float>(yj),
                                           static_cast<float>(zj), static_cast<float>(nj >> 11) * 2048.0f);
@@ -148,6 +163,7 @@ struct TcArgs {
     unsigned long long *d_count;
     float *d_sum;           // interaction sum (sum kernels only)
     double *partial;        // one FP64 slot per CTA (sum kernels only)
+    const float *px, *py, *pz, *pr;   // FP32 spheres: the caller's coordinates and radii
     uint64_t wait_ns;
     int32_t stall;          // test hook: the copy warp issues nothing
     int32_t pad;
@@ -188,6 +204,19 @@ __device__ __forceinline__ float term_f32(float d2) {
     return __frcp_rn(fmaxf(__fsqrt_rn(d2), 1e-6f));
 }
 
+// The FP32 sphere predicate, the same operations in the same order and rounding as the
+// FP32-pipe kernels (differences, squares and sums each rounded to nearest, never fused):
+// collide iff (dx*dx + dy*dy) + dz*dz <= (r_i + r_j)^2; d2 is returned for the term.
+__device__ __forceinline__ bool sphere_pair(float xi, float yi, float zi, float ri, float xj, float yj, float zj,
+                                            float rj, float &d2) {
+    const float dx = __fsub_rn(xi, xj);
+    const float dy = __fsub_rn(yi, yj);
+    const float dz = __fsub_rn(zi, zj);
+    d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    const float s = __fadd_rn(ri, rj);
+    return d2 <= __fmul_rn(s, s);
+}
+
 // Kahan's compensated summation: the error stays within (2u + O(k u^2)) times the sum of the
 // k (positive) terms, u = 2^-24, so FP32 serves for the whole kernel (k u^2 < 1e-8 for the
 // largest per-thread term counts) and the FP64 pipe, slow on this part, is kept off the
@@ -216,7 +245,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // a Kahan-compensated FP32 sum per thread. (Walking the register copy instead, with the
 // accumulator handed back at once, keeps all 128 values live through the walk: it spilled
 // and measured slower at every hit density.)
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false>
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false, bool SPH = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -225,7 +254,9 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     static_assert(CPW == 32 || CPW == 64 || CPW == 128, "one TMEM load per epilogue warp and unit");
     constexpr int kStage = L::kStage;
     extern __shared__ __align__(1024) uint8_t smem[];
-    if (A.hdr->mode != MODE_I32_TC) return;   // uniform: another kernel handles this call
+    // uniform: another kernel handles this call
+    if (A.hdr->mode != (SPH ? MODE_F32_TC : MODE_I32_TC)) return;
+    constexpr bool WALK = SUMT || SPH;   // screened values are walked one by one
 
     uint8_t *sA = smem + L::kA;
     uint8_t *sB = smem + L::kB;
@@ -418,7 +449,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             tc_fence_after();
             uint32_t v[CPW];
             tmem_ld<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
-            if (!SUMT) {
+            if (!WALK) {
                 // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
                 // before counting, so the next MMA overlaps this warp's arithmetic
                 tc_fence_before();
@@ -426,7 +457,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 if (lane == 0) mbar_arrive(&t_empty[buf]);
             }
             const bool full = eo0 >= TC_T && eo0 + JS - 1 <= A.h;
-            if (SUMT) {
+            if (WALK) {
                 // screen: any negative value (or -0) in the warp's block of the accumulator?
                 uint32_t orv = 0;
 #pragma unroll
@@ -442,6 +473,15 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                         gm |= (o8 >> 31) << g;
                     }
                     gm = __reduce_or_sync(0xFFFFFFFFu, gm);
+                    // spheres: this row's object (rows past n are never flagged)
+                    const int64_t io = t * TC_T + row;
+                    float xi = 0.0f, yi = 0.0f, zi = 0.0f, ri = 0.0f;
+                    if (SPH && io < A.n) {
+                        xi = A.px[io];
+                        yi = A.py[io];
+                        zi = A.pz[io];
+                        ri = A.pr[io];
+                    }
                     // walk the flagged groups exactly (compact code: one group at a time)
                     // columns c of this row that the schedule assigns: 1 <= d0 + c <= ev
                     int32_t clo = 0, cspan = CPW - 1;
@@ -479,8 +519,19 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                             uint32_t u = w[0];
 #pragma unroll
                             for (int k = 1; k < 8; ++k) u = j == k ? w[k] : u;
-                            ++cnt;
-                            kahan_add(ks, kc, term_f32(__fadd_rn(__uint_as_float(u), off_f)));
+                            if constexpr (SPH) {
+                                // screened pair: the FP32 predicate decides (column -> object)
+                                const int64_t e = io + (static_cast<int64_t>(eo0) + part * CPW + 8 * g + j - row);
+                                const int64_t jo = e < A.n ? e : e - A.n;
+                                float d2;
+                                if (sphere_pair(xi, yi, zi, ri, A.px[jo], A.py[jo], A.pz[jo], A.pr[jo], d2)) {
+                                    ++cnt;
+                                    if (SUMT) kahan_add(ks, kc, term_f32(d2));
+                                }
+                            } else {
+                                ++cnt;
+                                kahan_add(ks, kc, term_f32(__fadd_rn(__uint_as_float(u), off_f)));
+                            }
                         }
                     } while (gm);
                 }
@@ -605,10 +656,10 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false>
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false, bool SPH = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -631,7 +682,11 @@ static int tc_variant() {
     return v;
 }
 
-static cc_status tc_pick(TcLaunch &L, bool sum) {
+static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
+    if (sph) {
+        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true>(L)
+                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true>(L);
+    }
     if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true>(L);
     switch (tc_variant()) {
         case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
@@ -643,26 +698,33 @@ static cc_status tc_pick(TcLaunch &L, bool sum) {
 }
 
 // Enqueues the operand fill; it does nothing unless the preparation kernel chose
-// MODE_I32_TC for this call. `region` holds tc_region_bytes(n).
+// MODE_I32_TC (integer points) or MODE_F32_TC (spheres) for this call. `region` holds
+// tc_region_bytes(n).
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream) {
     TcLaunch L;
-    cc_status st = tc_pick(L, false);   // the sum kernel has the same stage width
+    cc_status st = tc_pick(L, false, false);   // every form has the same stage width
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
     const int64_t rows = std::max<int64_t>(g.M * TC_T, g.elen);
     const int blocks = static_cast<int>(std::min<int64_t>((rows + 255) / 256, static_cast<int64_t>(sm_count()) * 8));
-    k_fill_tc<<<blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x), static_cast<const int32_t *>(p->y),
-                                          static_cast<const int32_t *>(p->z), n, g.M * TC_T, g.elen, region,
-                                          region + g.a_bytes, hdr);
+    if (p->dtype == CC_F32) {
+        k_fill_tc<true><<<blocks, 256, 0, stream>>>(p->x, p->y, p->z, n, g.M * TC_T, g.elen, region,
+                                                    region + g.a_bytes, hdr);
+    } else {
+        k_fill_tc<false><<<blocks, 256, 0, stream>>>(p->x, p->y, p->z, n, g.M * TC_T, g.elen, region,
+                                                     region + g.a_bytes, hdr);
+    }
     CC_CUDA(cudaGetLastError());
     return CC_OK;
 }
 
-// Enqueues the tensor-core kernel (returns at once unless the mode is MODE_I32_TC).
-cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsigned long long *d_count,
-                           float *d_sum, double *partial, cudaStream_t stream) {
+// Enqueues the tensor-core kernel (returns at once unless the mode is MODE_I32_TC, or
+// MODE_F32_TC for spheres).
+cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region, WsHeader *hdr,
+                           unsigned long long *d_count, float *d_sum, double *partial, cudaStream_t stream) {
     TcLaunch L;
-    cc_status st = tc_pick(L, d_sum != nullptr);
+    const bool sph = p->dtype == CC_F32;
+    cc_status st = tc_pick(L, d_sum != nullptr, sph);
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
     TcArgs A;
@@ -676,6 +738,10 @@ cc_status tc_enqueue_pairs(int64_t n, const uint8_t *region, WsHeader *hdr, unsi
     A.d_count = d_count;
     A.d_sum = d_sum;
     A.partial = partial;
+    A.px = sph ? static_cast<const float *>(p->x) : nullptr;
+    A.py = sph ? static_cast<const float *>(p->y) : nullptr;
+    A.pz = sph ? static_cast<const float *>(p->z) : nullptr;
+    A.pr = sph ? p->r : nullptr;
     A.wait_ns = wait_limit_ns();
     A.stall = debug_stall();
     A.pad = 0;
