@@ -441,7 +441,7 @@ def main():
     if rank == 0 and not args.no_extras:
         line["fp32_pipe_step"] = bench_fp32_pipe_step(cc, torch, step, outs, want, tests_per_step,
                                                       roofline_peak_int(sms, fmax) / 1e9, flush)
-        line["f32_spheres"] = bench_f32(cc, torch, dev, sms, fmax, peak_src)
+        line["f32_spheres"] = bench_f32(cc, torch, dev, sms, fmax, peak_src, peaks)
         line["i32_sums"] = bench_i32_sums(cc, torch, dev)
         line["batched"] = bench_batched(cc, torch, dev)
         line["serving"] = bench_serving(cc, torch, dev, args.serving_queries)
@@ -503,28 +503,53 @@ def _time(fn, reps, torch, stream=None):
     return e0.elapsed_time(e1) / reps
 
 
-def bench_f32(cc, torch, dev, sms, fmax, peak_src):
+def bench_f32(cc, torch, dev, sms, fmax, peak_src, peaks):
+    """Config 3 (FP32 spheres): count and sum on the kernel the device chooses (the
+    tensor-core screen for this set) and on the FP32-pipe kernel; counts must agree."""
     c = synth.cfg3()
     n = len(c["x"])
     t = [torch.from_numpy(c[k]).to(dev) for k in ("x", "y", "z", "r")]
-    ms_c = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r=t[3]), 10, torch)
-    cc.profile_enable(True)
-    cc.profile_read()
-    ms_s = _time(lambda: cc.interaction_sum(t[0], t[1], t[2], r=t[3]), 10, torch)
-    kms, kl = cc.profile_read()
-    cc.profile_enable(False)
-    s, cnt = cc.interaction_sum(t[0], t[1], t[2], r=t[3])
-    torch.cuda.synchronize()
-    peak = roofline_peak_f32(sms, fmax) / 1e9
-    g_count = pairs(n) / (ms_c * 1e-3) / 1e9
-    return {"workload": f"N={n} FP32 spheres [0,1)^3 r in [0.001,0.004]",
-            "count_ms": ms_c, "count_gpairs_s": g_count,
-            "sum_ms": ms_s, "sum_gpairs_s": pairs(n) / (ms_s * 1e-3) / 1e9,
-            "count": cc.as_u64(cnt), "sum": float(s.item()),
-            "roofline_peak": peak, "count_frac": g_count / peak,
-            "issue_roofline_peak": issue_roofline(sms, fmax, 12),
-            "count_frac_of_issue_roofline": g_count / issue_roofline(sms, fmax, 12),
-            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src}) / 10 FP32 ops per pair"}
+    legs = {}
+    for tc in (True, False):
+        cc.set_tensor_cores(tc)
+        try:
+            ms_c = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r=t[3]), 10, torch)
+            cnt_c = cc.as_u64(cc.count_pairs(t[0], t[1], t[2], r=t[3]))
+            torch.cuda.synchronize()
+            mode = cc.stream_mode()
+            ms_s = _time(lambda: cc.interaction_sum(t[0], t[1], t[2], r=t[3]), 10, torch)
+            s, cnt = cc.interaction_sum(t[0], t[1], t[2], r=t[3])
+            torch.cuda.synchronize()
+        finally:
+            cc.set_tensor_cores(True)
+        g = pairs(n) / (ms_c * 1e-3) / 1e9
+        legs["tensor" if tc else "fp32_pipe"] = {
+            "mode": mode, "count_ms": ms_c, "count_gpairs_s": g, "sum_ms": ms_s,
+            "sum_gpairs_s": pairs(n) / (ms_s * 1e-3) / 1e9, "count": cnt_c, "sum_count": cc.as_u64(cnt),
+            "sum": float(s.item())}
+    tl, fl = legs["tensor"], legs["fp32_pipe"]
+    peak_fp32 = roofline_peak_f32(sms, fmax) / 1e9
+    peak_tc = float(peaks.get("bf16_tflops", 1900.0)) * TF32_PER_BF16 * 1e3 / TC_FLOPS_PER_PAIR   # G pair tests/s
+    chosen = tl if tl["mode"] == cc.MODE_TENSOR_SPHERES else fl
+    g_count = chosen["count_gpairs_s"]
+    out = {"workload": f"N={n} FP32 spheres [0,1)^3 r in [0.001,0.004]",
+           "kernel": "k_pairs_tc (integer screen + FP32 predicate)" if chosen is tl else "k_pairs_w (FP32 pipe)",
+           "count_ms": chosen["count_ms"], "count_gpairs_s": g_count,
+           "sum_ms": chosen["sum_ms"], "sum_gpairs_s": chosen["sum_gpairs_s"],
+           "count": chosen["count"], "sum": chosen["sum"],
+           "counts_equal": tl["count"] == fl["count"] == tl["sum_count"] == fl["sum_count"],
+           "sum_rel_diff": abs(tl["sum"] - fl["sum"]) / max(abs(fl["sum"]), 1e-30),
+           "tensor": tl, "fp32_pipe": fl,
+           "fp32_pipe_roofline_peak": peak_fp32, "fp32_pipe_count_frac": fl["count_gpairs_s"] / peak_fp32,
+           "issue_roofline_peak": issue_roofline(sms, fmax, 12),
+           "count_frac_of_issue_roofline": g_count / issue_roofline(sms, fmax, 12),
+           "peak_basis": (f"FP32 pipe: {sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz ({peak_src}) / 10 FP32 ops per "
+                          f"pair; tensor: {peak_tc:.0f} G pair tests/s = measured bf16 x {TF32_PER_BF16:.3f} / "
+                          f"{TC_FLOPS_PER_PAIR} TF32 flops per screened pair")}
+    if chosen is tl:
+        out["tensor_roofline_peak"] = peak_tc
+        out["tensor_count_frac"] = g_count / peak_tc
+    return out
 
 
 def bench_i32_sums(cc, torch, dev, n=262144):
@@ -581,17 +606,29 @@ def bench_linear(cc, torch, dev, peaks):
 def bench_schedules(cc, torch, dev, n=600_000):
     """The paper's GPU comparison (Section 5) restated on this GPU: balanced cyclic
     schedule vs the straightforward one (each group of 1024 objects against all later
-    objects), same records and inner loop, FP32 spheres of diameter 1, N > 525,000."""
+    objects), same records and inner loop on the FP32 pipe, FP32 spheres of diameter 1,
+    N > 525,000. The tensor-core screen's time on the same set is reported beside it."""
     x, y, z, r = synth.unit_spheres(n)
     t = [torch.from_numpy(a).to(dev) for a in (x, y, z, r)]
-    ms_cyc = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r=t[3]), 3, torch)
+    cc.set_tensor_cores(False)   # the schedule comparison runs one kernel family
+    try:
+        ms_cyc = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r=t[3]), 3, torch)
+        a = cc.count_pairs(t[0], t[1], t[2], r=t[3])
+        torch.cuda.synchronize()
+        mode_cyc = cc.stream_mode()
+    finally:
+        cc.set_tensor_cores(True)
     ms_str = _time(lambda: cc.count_pairs_straightforward(t[0], t[1], t[2], r=t[3]), 3, torch)
-    a = cc.count_pairs(t[0], t[1], t[2], r=t[3])
     b = cc.count_pairs_straightforward(t[0], t[1], t[2], r=t[3])
+    ms_tc = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r=t[3]), 3, torch)
+    c = cc.count_pairs(t[0], t[1], t[2], r=t[3])
     torch.cuda.synchronize()
+    mode_tc = cc.stream_mode()
     return {"workload": f"N={n} FP32 spheres of diameter 1, centres uniform in [0,200)^3",
             "cyclic_ms": ms_cyc, "straightforward_ms": ms_str, "speedup_cyclic": ms_str / ms_cyc,
-            "counts_equal": cc.as_u64(a) == cc.as_u64(b), "count": cc.as_u64(a),
+            "cyclic_mode": mode_cyc,
+            "counts_equal": cc.as_u64(a) == cc.as_u64(b) == cc.as_u64(c), "count": cc.as_u64(a),
+            "tensor_screen_ms": ms_tc, "tensor_screen_mode": mode_tc,
             "paper": "1.12x on a Tesla P100 (Section 5), context only"}
 
 

@@ -38,9 +38,8 @@ cc_status plan_launch_sets(cc_plan *P, int32_t n_sets, int32_t want_sum, unsigne
                            float *d_sums, cudaStream_t s);
 size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc);
 bool tc_enabled();
-// Integer sets at least this large have their count and sum queries served by the
-// single-set path (the tensor-core kernel when the set's range admits it) instead of the
-// batch.
+// Sets at least this large have their count and sum queries served by the single-set
+// path (a tensor-core kernel when the set admits it) instead of the batch.
 constexpr int64_t kServerTcMinN = 16384;
 void *plan_sets_buffer_v(cc_plan *P);
 size_t plan_set_desc_bytes();
@@ -214,18 +213,19 @@ static bool launch(cc_server *S, Lane &L) {
         cc_status st = e == cudaSuccess
                            ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
                            : CC_ERR_CUDA;
-        // queries on large integer sets: one single-set call each, stream-ordered after the
+        // queries on large sets: one single-set call each, stream-ordered after the
         // batch (this thread is the lane stream's only user, so its workspace is too)
         for (size_t j = 0; st == CC_OK && j < singles.size(); ++j) {
             const int32_t k = singles[j];
             const SetRec &sr = S->sets[L.batch[k].set_id];
             const size_t col = static_cast<size_t>(sr.n) * 4;
             cc_points pts;
-            pts.dtype = CC_I32;
+            pts.dtype = sr.dtype;
             pts.x = sr.buf;
             pts.y = static_cast<char *>(sr.buf) + col;
             pts.z = static_cast<char *>(sr.buf) + 2 * col;
-            pts.r = nullptr;
+            pts.r = sr.dtype == CC_F32 ? reinterpret_cast<const float *>(static_cast<char *>(sr.buf) + 3 * col)
+                                       : nullptr;
             st = L.batch[k].op == CC_OP_SUM
                      ? cc_interaction_sum(&pts, sr.n, L.batch[k].r2, L.d_sums + k, L.d_counts + k, L.stream)
                      : cc_count_pairs(&pts, sr.n, L.batch[k].r2, L.d_counts + k, L.stream);
@@ -322,7 +322,7 @@ cc_status cc_server_register_set(cc_server *S, const cc_points *p, int64_t n, in
         if (S->resident_bytes + S->inflight_bytes + bytes > S->budget)
             return fail(CC_ERR_NOMEM, "memory budget exceeded by this set");
         S->resident_bytes += bytes;
-        if (p->dtype == CC_I32 && n >= kServerTcMinN && tc_enabled()) {
+        if (n >= kServerTcMinN && tc_enabled()) {
             // both lanes may hold a workspace of this size (allocated by the scheduler on
             // first use); without room in the budget the set stays on the batched path
             const size_t need = 2 * std::max(single_ws_bytes(n, false, true), single_ws_bytes(n, true, true));

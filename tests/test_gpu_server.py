@@ -129,33 +129,38 @@ def test_cfg5_pool_sample(cc):
     srv.close()
 
 
-def test_large_integer_sets_in_the_mix(cc):
-    """Integer sets of n >= 16384: their count and sum queries run the single-set
-    (tensor-core) path stream-ordered after the batch; every count equals the oracle and
-    every sum the oracle's FP64 sum, alone and mixed with small sets and FP32 spheres."""
+def test_large_sets_in_the_mix(cc):
+    """Sets of n >= 16384 (integer points and FP32 spheres): their count and sum queries
+    run the single-set (tensor-core) path stream-ordered after the batch; every count
+    equals the oracle and every sum the oracle's FP64 sum to 1e-5, alone and mixed with
+    small sets."""
     rng = np.random.default_rng(21)
     sets = []
     for n, box in ((20000, 200), (30001, 1024), (16384, 64)):
         x, y, z = (rng.integers(0, box, n).astype(np.int32) for _ in range(3))
         sets.append(("i32", x, y, z, None))
+    for n, lo, hi in ((20001, 0.002, 0.01), (16400, 0.01, 0.03)):   # screened form; FP32-pipe fall-back
+        x, y, z = (rng.random(n, dtype=np.float32) for _ in range(3))
+        sets.append(("f32", x, y, z, (lo + (hi - lo) * rng.random(n)).astype(np.float32)))
     sets += pool(k=8, seed=22)
     srv = cc.Server(1 << 30, 64)
     ids = [srv.register_set(*s[1:4], r=s[4]) for s in sets]
     reqs = []
     for k, sid in enumerate(ids):
         reqs.append((sid, cc.CC_OP_COUNT, 9, 2 * k))
-        if sets[k][0] == "i32" and len(sets[k][1]) >= 16384:
+        if len(sets[k][1]) >= 16384:
             reqs.append((sid, cc.CC_OP_SUM, 9, 2 * k + 1))
     res = run_requests(srv, reqs)
     res2 = run_requests(srv, [(a, b, c, d + 10000) for (a, b, c, d) in reqs])
     for (sid, op, r2, rid) in reqs:
         k = rid // 2
-        want_c, _ = expected(sets[k], 9)
+        want_c, want_s = expected(sets[k], 9)
         assert res[rid]["status"] == 0 and res[rid]["count"] == want_c, (k, op)
         assert res2[rid + 10000]["count"] == want_c
         if op == cc.CC_OP_SUM:
-            c2, want_s = oracle.sum_i32(*sets[k][1:4], 9)
-            assert c2 == want_c
+            if sets[k][0] == "i32":
+                c2, want_s = oracle.sum_i32(*sets[k][1:4], 9)
+                assert c2 == want_c
             for r in (res[rid], res2[rid + 10000]):
                 assert abs(r["sum"] - want_s) <= 1e-5 * want_s, (k, r["sum"], want_s)
     srv.close()
