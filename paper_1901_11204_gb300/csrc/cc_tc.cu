@@ -458,11 +458,16 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             }
             const bool full = eo0 >= TC_T && eo0 + JS - 1 <= A.h;
             if (WALK) {
-                // screen: any negative value (or -0) in the warp's block of the accumulator?
-                uint32_t orv = 0;
+                // screen: any negative value in the warp's block of the accumulator? The
+                // rounding-down FMA of the count kernel on fresh accumulators (the FMA pipe
+                // measured faster here than an OR screen on the ALU pipe)
+                f2 sa[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
 #pragma unroll
-                for (int j = 0; j < CPW; j += 2) orv |= v[j] | v[j + 1];
-                if (__any_sync(0xFFFFFFFFu, orv & 0x80000000u)) {
+                for (int j = 0; j < CPW / 2; ++j) {
+                    const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
+                    sa[j & 3] = f2_fma_rm(pv, kScale, sa[j & 3]);
+                }
+                if (__any_sync(0xFFFFFFFFu, (sa[0] & sa[1] & sa[2] & sa[3]) != kAccInit)) {
                     // one bit per group of 8 columns holding one, warp-uniform
                     uint32_t gm = 0;
 #pragma unroll
