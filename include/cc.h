@@ -134,9 +134,9 @@ cc_status cc_stream_status(void *stream);
  *   CC_MODE_RANGE_ERROR  span above 32767: nothing was counted
  *   CC_MODE_FP32_SPHERES FP32 spheres
  *   CC_MODE_TENSOR       integer points, the same exact form as a TF32 tensor-core
- *                        contraction (n >= 16384, and only while the absolute values
+ *                        contraction (n >= 8192, and only while the absolute values
  *                        of its eight terms sum to less than 2^24)
- *   CC_MODE_TENSOR_SPHERES FP32 spheres, n >= 16384: an exact integer screen of
+ *   CC_MODE_TENSOR_SPHERES FP32 spheres, n >= 8192: an exact integer screen of
  *                        quantised coordinates on the tensor cores passes every pair
  *                        that can collide, and the FP32 predicate above decides each
  *                        screened pair (all coordinates and radii finite, and the

@@ -41,8 +41,17 @@ bool tc_enabled();
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream);
 cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region, WsHeader *hdr,
                            unsigned long long *d_count, float *d_sum, double *partial, cudaStream_t stream);
-// Smallest set for which counts take the tensor-core kernel.
-constexpr int64_t TC_MIN_N = 16384;
+// Smallest set for which counts and sums take a tensor-core form: 8192 objects (the
+// measured crossover: at 8192 both forms take about 33 us per call, at 12288 the tensor
+// cores 25-30 % less), or the environment variable CC_TC_MIN_N (read once).
+int64_t tc_min_n() {
+    static int64_t v = -1;
+    if (v < 0) {
+        const char *e = getenv("CC_TC_MIN_N");
+        v = (e && atoll(e) >= 2) ? static_cast<int64_t>(atoll(e)) : 8192;
+    }
+    return v;
+}
 
 // ---------------------------------------------------------------------------------------
 // preparation kernels
@@ -868,7 +877,7 @@ static cc_status pick_launch(int64_t n, bool f32, bool sum, Launch &L) {
 
 static bool use_tc(int64_t n, bool sum, bool allow_tc) {
     (void)sum;   // counts and interaction sums alike
-    return allow_tc && n >= TC_MIN_N && tc_enabled();
+    return allow_tc && n >= tc_min_n() && tc_enabled();
 }
 
 // Workspace layout: WsHeader | region | double partial[grid], where the region holds

@@ -18,7 +18,7 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TC_MIN_N = 16384
+TC_MIN_N = 8192
 
 
 @pytest.fixture(scope="module")
@@ -142,7 +142,7 @@ def test_all_points_identical(cc):
     assert got == n * (n - 1) // 2
 
 
-@pytest.mark.parametrize("n", [16384, 16385, 16511, 16512, 16513, 33025, 65791])
+@pytest.mark.parametrize("n", [8192, 8193, 16384, 16385, 16511, 16512, 16513, 33025, 65791])
 def test_ragged_sizes(cc, n):
     rng = np.random.default_rng(n)
     x, y, z = box_points(rng, n, 1023)

@@ -17,7 +17,7 @@ from tests.golden import make_near_ties as nt
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TC_MIN_N = 16384
+TC_MIN_N = 8192
 SUM_RTOL = 1e-5
 
 
@@ -61,7 +61,7 @@ def check(cc, x, y, z, r, want_mode):
     return c, s
 
 
-@pytest.mark.parametrize("n", [16384, 16385, 20001, 33026])
+@pytest.mark.parametrize("n", [8192, 8193, 16384, 16385, 20001, 33026])
 def test_counts_and_sums_on_tensor_cores(cc, n):
     rng = np.random.default_rng(300 + n)
     x, y, z, r = spheres(rng, n)
