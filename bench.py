@@ -231,6 +231,7 @@ def roofline_peak_int(sms: int, mhz: float) -> float:
 
 # Tensor-core form: one TF32 contraction of K = 8 terms per pair test (16 flops).
 TC_FLOPS_PER_PAIR = 16
+TMEM_READ_BYTES_PER_CLK = 350   # measured TMEM->register rate per SM, eight warps of 16 KB loads
 # TF32 / BF16 dense tensor throughput ratio of the part's nominal figures (1.1 / 2.25 PF).
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -354,6 +355,15 @@ def main():
             "kernel_launches": kern_launches,
             "timing_note": "events bracket the tensor-core launch and the FP32-pipe launch that "
                            "returns at once in tensor mode",
+        }
+        # The accumulator of every pair test is read back from TMEM (4 B per pair): the
+        # read rate measured on this GPU with the kernel's load shape is the tighter bound.
+        tmem_peak = sms * TMEM_READ_BYTES_PER_CLK * fmax * 1e6 / 4.0 / 1e9   # G pair tests/s
+        roofline["tmem_read_bound"] = {
+            "peak_pair_tests_per_s": tmem_peak,
+            "frac": (pair_rate / tmem_peak) if pair_rate else None,
+            "basis": (f"{TMEM_READ_BYTES_PER_CLK} B/clk/SM TMEM-to-register reads measured with eight warps of "
+                      f"32x32b.x128 loads, x {sms} SMs x {fmax:.0f} MHz, 4 B of accumulator per pair test"),
         }
     else:
         traffic, traffic_note = measured_traffic("fp32")
