@@ -238,14 +238,22 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // each j-stage slot and each i-tile slot (plain arrivals once it has seen the completion
 // of the MMAs that read them), leaving the MMA thread one commit per unit. The MMA
 // thread is the pipeline's critical path (it shares its SMSP with two counting warps);
-// both measured faster and are on in the default shape. SUMT: the interaction sum as well.
-// Every value is screened with the ALU OR; where the warp holds a hit, the groups of 8
-// columns that hold one are re-read from TMEM and walked exactly before the accumulator is
-// handed back, counting and adding 1/max(d, 1e-6) with d^2 = v + r2e + 1 exact in FP32, in
-// a Kahan-compensated FP32 sum per thread. (Walking the register copy instead, with the
-// accumulator handed back at once, keeps all 128 values live through the walk: it spilled
-// and measured slower at every hit density.)
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false, bool SPH = false>
+// both measured faster and are on in the default shape.
+// RED (default): the accumulator is read with tcgen05.ld.red .min, which also gives each
+// thread the minimum of its 128 values; a warp whose minimum is non-negative everywhere
+// (every pair of the block misses) skips the count, so the FMA-pipe counting runs only
+// for warps that hold a hit (+30 % at low hit density, +4 % at one hit per 30,000 pairs).
+// WALKC: such warps count by the walk below instead (faster only for very rare hits).
+// SUMT: the interaction sum as well; SPH: FP32 spheres, the integer form being a screen.
+// Where the warp holds a negative value, the groups of 8 columns that hold one are
+// re-read from TMEM and walked exactly before the accumulator is handed back: for sums,
+// counting and adding 1/max(d, 1e-6) with d^2 = v + r2e + 1 exact in FP32, in a
+// Kahan-compensated FP32 sum per thread; for spheres, applying the FP32 predicate to the
+// pair's own coordinates. (Walking the register copy instead, with the accumulator
+// handed back at once, keeps all 128 values live through the walk: it spilled and
+// measured slower at every hit density.)
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
+          bool SPH = false, bool RED = false, bool WALKC = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     extern __shared__ __align__(1024) uint8_t smem[];
     // uniform: another kernel handles this call
     if (A.hdr->mode != (SPH ? MODE_F32_TC : MODE_I32_TC)) return;
-    constexpr bool WALK = SUMT || SPH;   // screened values are walked one by one
+    constexpr bool WALK = SUMT || SPH || WALKC;   // screened values are walked one by one
 
     uint8_t *sA = smem + L::kA;
     uint8_t *sB = smem + L::kB;
@@ -448,7 +456,15 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             }
             tc_fence_after();
             uint32_t v[CPW];
-            tmem_ld<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
+            float vmin = -1.0f;   // RED: the minimum of this thread's values
+            if constexpr (RED) {
+                vmin = tmem_ld_min<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
+            } else {
+                tmem_ld<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
+            }
+            // RED: does any lane of the warp hold a negative value? (warp-uniform skip)
+            bool warp_neg = true;
+            if constexpr (RED && !WALK) warp_neg = __any_sync(0xFFFFFFFFu, vmin < 0.0f);
             if (!WALK) {
                 // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
                 // before counting, so the next MMA overlaps this warp's arithmetic
@@ -461,13 +477,19 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 // screen: any negative value in the warp's block of the accumulator? The
                 // rounding-down FMA of the count kernel on fresh accumulators (the FMA pipe
                 // measured faster here than an OR screen on the ALU pipe)
-                f2 sa[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
+                bool any_neg;
+                if constexpr (RED) {
+                    any_neg = __any_sync(0xFFFFFFFFu, vmin < 0.0f);
+                } else {
+                    f2 sa[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
 #pragma unroll
-                for (int j = 0; j < CPW / 2; ++j) {
-                    const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
-                    sa[j & 3] = f2_fma_rm(pv, kScale, sa[j & 3]);
+                    for (int j = 0; j < CPW / 2; ++j) {
+                        const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
+                        sa[j & 3] = f2_fma_rm(pv, kScale, sa[j & 3]);
+                    }
+                    any_neg = __any_sync(0xFFFFFFFFu, (sa[0] & sa[1] & sa[2] & sa[3]) != kAccInit);
                 }
-                if (__any_sync(0xFFFFFFFFu, (sa[0] & sa[1] & sa[2] & sa[3]) != kAccInit)) {
+                if (any_neg) {
                     // one bit per group of 8 columns holding one, warp-uniform
                     uint32_t gm = 0;
 #pragma unroll
@@ -518,6 +540,10 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                         for (int j = 0; j < 8; ++j)
                             ok |= static_cast<uint32_t>(8 * g + j - clo) <= static_cast<uint32_t>(cspan) ? (1u << j) : 0u;
                         m8 &= ok;
+                        if constexpr (!SPH && !SUMT) {   // a count needs only how many
+                            cnt += __popc(m8);
+                            m8 = 0;
+                        }
                         while (m8) {
                             const int j = __ffs(m8) - 1;
                             m8 &= m8 - 1;
@@ -535,7 +561,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                                 }
                             } else {
                                 ++cnt;
-                                kahan_add(ks, kc, term_f32(__fadd_rn(__uint_as_float(u), off_f)));
+                                if (SUMT) kahan_add(ks, kc, term_f32(__fadd_rn(__uint_as_float(u), off_f)));
                             }
                         }
                     } while (gm);
@@ -548,10 +574,13 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 if (full) {
                     constexpr int NF = CPW - SCR;   // values counted on the FP32 pipe
                     static_assert(SCR % 2 == 0 && NF % 8 == 0, "split of the values");
+                    // RED: only warps holding a negative value count
+                    if (warp_neg) {
 #pragma unroll
-                    for (int j = 0; j < NF / 2; ++j) {
-                        const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
-                        acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
+                        for (int j = 0; j < NF / 2; ++j) {
+                            const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
+                            acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
+                        }
                     }
                     if constexpr (SCR > 0) {
                         uint32_t orv = 0;
@@ -562,7 +591,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                             for (int j = NF; j < CPW; ++j) cnt += __uint_as_float(v[j]) < 0.0f ? 1u : 0u;
                         }
                     }
-                } else {
+                } else if (warp_neg) {
                     const int64_t i = t * TC_T + row;
                     const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
                     const int64_t d0 = static_cast<int64_t>(eo0) + part * CPW - row;   // e - i of column 0
@@ -661,10 +690,11 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false, bool SPH = false>
+template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
+          bool SPH = false, bool RED = false, bool WALKC = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -682,23 +712,29 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 4) v = 0;
+        if (v < 0 || v > 6) v = 0;
     }
     return v;
 }
 
 static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
+    // Template arguments: stage width JS, accumulators NB, epilogue warps EPW, ring depth NS,
+    // values screened on the ALU SCR, early barrier tests PRE, epilogue slot returns STEW,
+    // interaction sum SUMT, sphere screen SPH, min-reducing TMEM loads RED, count by walk
+    // WALKC. Sums and spheres walk the screened values; counts take CC_TC_VARIANT.
     if (sph) {
-        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true>(L)
-                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true>(L);
+        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true>(L)
+                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true>(L);
     }
-    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true>(L);
+    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true>(L);
     switch (tc_variant()) {
         case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
         case 2: return tc_launch_of<128, 4, 8, 16, 0, true, true>(L);
         case 3: return tc_launch_of<256, 2, 16, 12, 0, true, true>(L);
         case 4: return tc_launch_of<256, 2, 8, 12, 64, true, true>(L);
-        default: return tc_launch_of<256, 2, 8, 12, 0, true, true>(L);
+        case 5: return tc_launch_of<256, 2, 8, 12, 0, true, true>(L);   // every value counted by FMA
+        case 6: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true>(L);
+        default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true>(L);
     }
 }
 
