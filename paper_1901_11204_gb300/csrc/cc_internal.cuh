@@ -163,6 +163,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// Waits for phase `parity` like mbar_wait_bounded, with try_wait's own (system-defined)
+// suspend time instead of a hint: the warp leaves the issue slots to the other warps of
+// its SMSP and resumes when the phase completes.
+__device__ __forceinline__ bool mbar_try_wait_nohint(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_sleep_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                                   const volatile int *abort = nullptr) {
+    if (mbar_try_wait_nohint(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait_nohint(bar, parity)) return true;
+        if (abort && *abort) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // Non-blocking test of phase `parity` (never suspends the thread).
 __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;

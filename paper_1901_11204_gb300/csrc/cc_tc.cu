@@ -253,7 +253,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // handed back at once, keeps all 128 values live through the walk: it spilled and
 // measured slower at every hit density.)
 template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
-          bool SPH = false, bool RED = false, bool WALKC = false>
+          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -330,13 +330,17 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             for (; q < nu; ++q) {
                 if (t != cur_t) {
                     const uint32_t as = na & 1u;
-                    if (!mbar_spin_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
+                    if (!(TRYW ? mbar_sleep_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)
+                               : mbar_spin_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)))
+                        break;
                     mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
                     bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
                     ++na;
                     cur_t = t;
                 }
-                if (!mbar_spin_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)) break;
+                if (!(TRYW ? mbar_sleep_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)
+                           : mbar_spin_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)))
+                    break;
                 mbar_arrive_expect_tx(&b_full[slot], kStage);
                 bulk_g2s(sB + slot * kStage, bsrc, kStage, &b_full[slot]);
                 bsrc += JS * TC_ROW;
@@ -440,7 +444,8 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         for (int32_t q = 0; q < nu; ++q) {
             const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
-            const bool got = __all_sync(0xFFFFFFFFu, mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
+            const bool got = __all_sync(0xFFFFFFFFu, TRYW ? mbar_sleep_bounded(&t_full[buf], fph, A.wait_ns, abort_flag)
+                                                          : mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
                     atomicOr(&A.hdr->status, ST_TIMEOUT);
@@ -691,10 +696,10 @@ struct TcLaunch {
 };
 
 template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
-          bool SPH = false, bool RED = false, bool WALKC = false>
+          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC, TRYW>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -712,7 +717,7 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 6) v = 0;
+        if (v < 0 || v > 7) v = 0;
     }
     return v;
 }
@@ -721,12 +726,13 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
     // Template arguments: stage width JS, accumulators NB, epilogue warps EPW, ring depth NS,
     // values screened on the ALU SCR, early barrier tests PRE, epilogue slot returns STEW,
     // interaction sum SUMT, sphere screen SPH, min-reducing TMEM loads RED, count by walk
-    // WALKC. Sums and spheres walk the screened values; counts take CC_TC_VARIANT.
+    // WALKC, sleeping waits in the epilogue and copy warps TRYW. Sums and spheres walk the
+    // screened values; counts take CC_TC_VARIANT.
     if (sph) {
-        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true>(L)
-                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true>(L);
+        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true>(L)
+                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true>(L);
     }
-    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true>(L);
+    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true, false, true>(L);
     switch (tc_variant()) {
         case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
         case 2: return tc_launch_of<128, 4, 8, 16, 0, true, true>(L);
@@ -734,7 +740,8 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
         case 4: return tc_launch_of<256, 2, 8, 12, 64, true, true>(L);
         case 5: return tc_launch_of<256, 2, 8, 12, 0, true, true>(L);   // every value counted by FMA
         case 6: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true>(L);
-        default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true>(L);
+        case 7: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true>(L);   // spinning waits
+        default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true>(L);
     }
 }
 
