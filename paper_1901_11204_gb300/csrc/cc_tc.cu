@@ -234,7 +234,8 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // values; a set sign bit sends that group to an exact recount, rare unless hits are
 // dense) and the rest counted exactly on the FP32 pipe, so the two pipes share the work.
 // PRE: the MMA thread tests the next unit's barriers right after issuing the current
-// MMA, before its commits. STEW: the first epilogue thread, not the MMA thread, returns
+// MMA (CF: after committing the accumulator's barrier, so that the epilogue hears of the
+// MMA sooner; otherwise before the commits). STEW: the first epilogue thread, not the MMA thread, returns
 // each j-stage slot and each i-tile slot (plain arrivals once it has seen the completion
 // of the MMAs that read them), leaving the MMA thread one commit per unit. The MMA
 // thread is the pipeline's critical path (it shares its SMSP with two counting warps);
@@ -253,7 +254,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // handed back at once, keeps all 128 values live through the walk: it spilled and
 // measured slower at every hit density.)
 template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
-          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false>
+          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false, bool CF = false>
 __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     using L = TcSmem<JS, NB, EPW, NS>;
     static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
@@ -407,12 +408,13 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     buf = 0;
                     eph ^= 1u;
                 }
+                if (CF) tc_commit(&t_full[cbuf]);   // the epilogue's barrier first
                 if (PRE) {
                     pre_full = mbar_test_wait(&b_full[slot], fph);
                     pre_empty = mbar_test_wait(&t_empty[buf], eph);
                 }
                 if (!STEW) tc_commit(&b_empty[cslot]);
-                tc_commit(&t_full[cbuf]);
+                if (!CF) tc_commit(&t_full[cbuf]);
                 if (!STEW && (new_tile || q + 1 == nu)) tc_commit(&a_empty[as]);
             }
             if (!ok) {
@@ -696,10 +698,10 @@ struct TcLaunch {
 };
 
 template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
-          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false>
+          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false, bool CF = false>
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC, TRYW>;
+    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC, TRYW, CF>;
     static bool attr = false;
     if (!attr) {
         CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
@@ -717,7 +719,7 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 7) v = 0;
+        if (v < 0 || v > 8) v = 0;
     }
     return v;
 }
@@ -726,13 +728,14 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
     // Template arguments: stage width JS, accumulators NB, epilogue warps EPW, ring depth NS,
     // values screened on the ALU SCR, early barrier tests PRE, epilogue slot returns STEW,
     // interaction sum SUMT, sphere screen SPH, min-reducing TMEM loads RED, count by walk
-    // WALKC, sleeping waits in the epilogue and copy warps TRYW. Sums and spheres walk the
-    // screened values; counts take CC_TC_VARIANT.
+    // WALKC, sleeping waits in the epilogue and copy warps TRYW, the accumulator's commit
+    // before the early barrier tests CF. Sums and spheres walk the screened values;
+    // counts take CC_TC_VARIANT.
     if (sph) {
-        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true>(L)
-                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true>(L);
+        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true, true>(L)
+                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true, true>(L);
     }
-    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true, false, true>(L);
+    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true, false, true, true>(L);
     switch (tc_variant()) {
         case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
         case 2: return tc_launch_of<128, 4, 8, 16, 0, true, true>(L);
@@ -741,7 +744,8 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
         case 5: return tc_launch_of<256, 2, 8, 12, 0, true, true>(L);   // every value counted by FMA
         case 6: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true>(L);
         case 7: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true>(L);   // spinning waits
-        default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true>(L);
+        case 8: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true>(L);   // commit after the tests
+        default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true, true>(L);
     }
 }
 
