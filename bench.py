@@ -439,9 +439,9 @@ def main():
         "roofline": roofline,
         "issue_roofline": issue_roofline_line,
         "e2e": e2e,
-        # per count: reset, min/max + mode, record fill, operand fill, tensor-core kernel and
-        # FP32-pipe kernel (the kernel and fill of the mode not chosen return at once)
-        "gpu_launches": (6 if tensor else 4) * len(sets) * args.steps,
+        # per count: reset, min/max + mode, record fill, operand fill, the two tensor-core
+        # count forms and the FP32-pipe kernel (the kernels and fill not chosen return at once)
+        "gpu_launches": (7 if tensor else 4) * len(sets) * args.steps,
         "pair_kernel_modes": modes,
         "clocks": clocks,
         "wall_s_timed_region": wall,

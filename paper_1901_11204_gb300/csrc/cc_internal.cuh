@@ -67,7 +67,9 @@ struct WsHeader {
     uint32_t qbad;        // ... non-zero when a coordinate or radius is not finite
     uint32_t qrmax;       // ... largest |radius| (bits of a non-negative float)
     double qscale;        // ... quantisation scale, 2046 / the largest per-axis span
-    uint32_t pad[10];
+    int32_t tc_form;      // integer tensor-core count: 0 = count blocks in registers,
+                          // 1 = walk the (rare) blocks with a hit (sparse hits expected)
+    uint32_t pad[9];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 static_assert(int{MODE_I32_FAST} == int{CC_MODE_FP32_EXACT} && int{MODE_I32_WIDE} == int{CC_MODE_INT_WIDE} &&

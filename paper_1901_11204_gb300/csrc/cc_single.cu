@@ -75,6 +75,11 @@ __global__ void k_reset(WsHeader *h, int32_t mode, unsigned long long *d_count, 
     }
 }
 
+// Expected hits per pair below which the integer tensor-core count walks hit blocks
+// instead of counting every block in registers (the measured crossover lies between
+// 1e-7 and 3e-5 hits per pair on uniform sets).
+constexpr double TC_SPARSE_HITS = 2e-6;
+
 // Per-axis min/max of the integer coordinates; the last block to finish derives the
 // execution mode, the integer centre and the clamped r2 (no spin: last-block ticket).
 __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
@@ -138,6 +143,18 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
     }
     int64_t r2e = static_cast<int64_t>(r2) < dmax ? static_cast<int64_t>(r2) : dmax;
     if (mode == MODE_I32_FAST && allow_tc && tc_exact(m, r2e)) mode = MODE_I32_TC;
+    // Which tensor-core count form: the expected hits per pair of a set spread uniformly
+    // over its bounding box, (lattice points within the r2 ball) / (box sites), bounded
+    // above by the ball of radius sqrt(r2) + 1. Below TC_SPARSE_HITS the walk form (a lean
+    // loop; measured +9 % at 1e-7) runs, above it the in-register count (+19 % at 3e-5).
+    // Either form gives the exact count; only the speed depends on the choice.
+    {
+        const double rad = sqrt(static_cast<double>(r2e)) + 1.0;
+        const double ball = 4.18879020478639 * rad * rad * rad;   // (4/3) pi rad^3
+        const double sites = static_cast<double>(span[0] + 1) * static_cast<double>(span[1] + 1) *
+                             static_cast<double>(span[2] + 1);
+        h->tc_form = ball < TC_SPARSE_HITS * sites ? 1 : 0;
+    }
     h->r2e = static_cast<uint32_t>(r2e);
     h->ai_off = static_cast<int32_t>(r2e + 1);
     h->mode = mode;

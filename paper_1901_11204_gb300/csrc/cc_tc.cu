@@ -166,7 +166,8 @@ struct TcArgs {
     const float *px, *py, *pz, *pr;   // FP32 spheres: the caller's coordinates and radii
     uint64_t wait_ns;
     int32_t stall;          // test hook: the copy warp issues nothing
-    int32_t pad;
+    int32_t form;           // integer counts: run only when the header's tc_form equals
+                            // this (0 or 1); -1 runs whatever the form
 };
 
 template <int JS, int NB, int EPW, int NS>
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     extern __shared__ __align__(1024) uint8_t smem[];
     // uniform: another kernel handles this call
     if (A.hdr->mode != (SPH ? MODE_F32_TC : MODE_I32_TC)) return;
+    if (A.form >= 0 && A.hdr->tc_form != A.form) return;   // the other count form runs
     constexpr bool WALK = SUMT || SPH || WALKC;   // screened values are walked one by one
 
     uint8_t *sA = smem + L::kA;
@@ -719,7 +721,7 @@ static int tc_variant() {
     if (v < 0) {
         const char *e = getenv("CC_TC_VARIANT");
         v = e ? atoi(e) : 0;
-        if (v < 0 || v > 8) v = 0;
+        if (v < 0 || v > 9) v = 0;
     }
     return v;
 }
@@ -745,6 +747,7 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
         case 6: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true>(L);
         case 7: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true>(L);   // spinning waits
         case 8: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true>(L);   // commit after the tests
+        case 9: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true, true, true>(L);   // walk form only
         default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true, true>(L);
     }
 }
@@ -796,9 +799,21 @@ cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region,
     A.pr = sph ? p->r : nullptr;
     A.wait_ns = wait_limit_ns();
     A.stall = debug_stall();
-    A.pad = 0;
+    A.form = -1;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g.units, sm_count())));
     void *args[] = {&A};
+    if (!sph && d_sum == nullptr && tc_variant() == 0) {
+        // integer count, default shape: both count forms are launched and the one the
+        // preparation kernel chose (hdr->tc_form, from the expected hit density) runs
+        TcLaunch W;
+        st = tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true, true, true>(W);
+        if (st != CC_OK) return st;
+        A.form = 0;
+        CC_CUDA(cudaLaunchKernel(L.fn, dim3(grid), dim3(L.threads), args, TC_SMEM_REQ, stream));
+        A.form = 1;
+        CC_CUDA(cudaLaunchKernel(W.fn, dim3(grid), dim3(W.threads), args, TC_SMEM_REQ, stream));
+        return CC_OK;
+    }
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(grid), dim3(L.threads), args, TC_SMEM_REQ, stream));
     return CC_OK;
 }
