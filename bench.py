@@ -192,11 +192,17 @@ TRAFFIC_FILES = {"fp32": "k_pairs_traffic.json", "tensor": "k_pairs_tc_traffic.j
 
 
 def kernel_source_hash(kind: str = "fp32") -> str:
+    """Hash of the kernel sources with comments and blank space removed: the DRAM counters
+    of a capture stay valid while the code they measured is unchanged."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES[kind]:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).encode())
     return h.hexdigest()
 
 

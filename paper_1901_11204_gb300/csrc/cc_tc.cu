@@ -236,16 +236,20 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // dense) and the rest counted exactly on the FP32 pipe, so the two pipes share the work.
 // PRE: the MMA thread tests the next unit's barriers right after issuing the current
 // MMA (CF: after committing the accumulator's barrier, so that the epilogue hears of the
-// MMA sooner; otherwise before the commits). STEW: the first epilogue thread, not the MMA thread, returns
-// each j-stage slot and each i-tile slot (plain arrivals once it has seen the completion
-// of the MMAs that read them), leaving the MMA thread one commit per unit. The MMA
+// MMA sooner; otherwise before the commits). STEW: the first epilogue thread, not the
+// MMA thread, returns each j-stage slot and each i-tile slot (plain arrivals once it has
+// seen the completion of the MMAs that read them), leaving the MMA thread one commit per
+// unit. The MMA
 // thread is the pipeline's critical path (it shares its SMSP with two counting warps);
 // both measured faster and are on in the default shape.
 // RED (default): the accumulator is read with tcgen05.ld.red .min, which also gives each
 // thread the minimum of its 128 values; a warp whose minimum is non-negative everywhere
 // (every pair of the block misses) skips the count, so the FMA-pipe counting runs only
 // for warps that hold a hit (+30 % at low hit density, +4 % at one hit per 30,000 pairs).
-// WALKC: such warps count by the walk below instead (faster only for very rare hits).
+// WALKC: such warps count by the walk below instead; no value then stays live past the
+// load, a leaner loop that is 9 % faster at 1e-7 hits per pair and 19 % slower at 3e-5.
+// The host launches both count forms and each runs only when the preparation kernel
+// chose it (hdr->tc_form, from the expected hit density; TcArgs::form).
 // SUMT: the interaction sum as well; SPH: FP32 spheres, the integer form being a screen.
 // Where the warp holds a negative value, the groups of 8 columns that hold one are
 // re-read from TMEM and walked exactly before the accumulator is handed back: for sums,
@@ -732,7 +736,8 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
     // interaction sum SUMT, sphere screen SPH, min-reducing TMEM loads RED, count by walk
     // WALKC, sleeping waits in the epilogue and copy warps TRYW, the accumulator's commit
     // before the early barrier tests CF. Sums and spheres walk the screened values;
-    // counts take CC_TC_VARIANT.
+    // counts take CC_TC_VARIANT (0: the in-register form here, launched beside the walk
+    // form by tc_enqueue_pairs, the device choosing between them).
     if (sph) {
         return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true, true>(L)
                    : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true, true>(L);
