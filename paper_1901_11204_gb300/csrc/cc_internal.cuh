@@ -52,6 +52,15 @@ enum : int32_t {
                          // FP32 predicate for the screened pairs
 };
 
+// Cells of the occupancy histogram (16 per axis over the bounding box) from which the
+// integer tensor-core path estimates its expected hits per pair.
+constexpr int TC_HIST_CELLS = 16 * 16 * 16;
+constexpr int TC_HIST_STRIDE = 8;   // one object in 8 enters the histogram
+// Expected hits per pair below which the integer tensor-core count walks hit blocks
+// instead of counting every block in registers (the measured crossover lies between
+// 1e-7 and 3e-5 hits per pair on uniform sets).
+constexpr double TC_SPARSE_HITS = 2e-6;
+
 // Workspace header: lives at the start of each stream's scratch buffer.
 struct WsHeader {
     uint32_t umin[3];     // order-preserving encodings of the per-axis minimum

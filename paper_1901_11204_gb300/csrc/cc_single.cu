@@ -2,7 +2,7 @@
 // algorithm, with the even-N extra step), lifted to tiles for sm_103a.
 //
 // Layout in HBM (per call, in the stream's workspace):
-//   WsHeader | Rec E[nrec] | double partial[grid]
+//   WsHeader | Rec E[nrec] | double partial[grid] | uint32 hist[TC_HIST_CELLS]
 // E is the "extended" sequence E[e] = P[e mod n] for e in [0, 2*nrec), stored as
 // pair-interleaved 32-byte records {x0,x1,y0,y1,z0,z1,w0,w1} so that (a) every j-range
 // of the cyclic schedule is one contiguous, 32-byte aligned span (no modulo in the hot
@@ -38,7 +38,8 @@ namespace cc {
 // tensor-core path (cc_tc.cu)
 size_t tc_region_bytes(int64_t n);
 bool tc_enabled();
-cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream);
+cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, uint32_t *hist,
+                          cudaStream_t stream);
 cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region, WsHeader *hdr,
                            unsigned long long *d_count, float *d_sum, double *partial, cudaStream_t stream);
 // Smallest set for which counts and sums take a tensor-core form: 8192 objects (the
@@ -75,16 +76,16 @@ __global__ void k_reset(WsHeader *h, int32_t mode, unsigned long long *d_count, 
     }
 }
 
-// Expected hits per pair below which the integer tensor-core count walks hit blocks
-// instead of counting every block in registers (the measured crossover lies between
-// 1e-7 and 3e-5 hits per pair on uniform sets).
-constexpr double TC_SPARSE_HITS = 2e-6;
-
 // Per-axis min/max of the integer coordinates; the last block to finish derives the
 // execution mode, the integer centre and the clamped r2 (no spin: last-block ticket).
 __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
                          const int32_t *__restrict__ z, int64_t n, uint32_t r2, WsHeader *h,
-                         unsigned long long *d_count, int32_t allow_tc) {
+                         unsigned long long *d_count, int32_t allow_tc, uint32_t *hist) {
+    // tensor-core path: clear the occupancy histogram the operand fill builds
+    if (hist)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < TC_HIST_CELLS;
+             i += (int64_t)gridDim.x * blockDim.x)
+            hist[i] = 0u;
     uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
     uint32_t mx[3] = {0u, 0u, 0u};
     const int32_t *c[3] = {x, y, z};
@@ -143,10 +144,11 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
     }
     int64_t r2e = static_cast<int64_t>(r2) < dmax ? static_cast<int64_t>(r2) : dmax;
     if (mode == MODE_I32_FAST && allow_tc && tc_exact(m, r2e)) mode = MODE_I32_TC;
-    // Which tensor-core count form: the expected hits per pair of a set spread uniformly
-    // over its bounding box, (lattice points within the r2 ball) / (box sites), bounded
-    // above by the ball of radius sqrt(r2) + 1. Below TC_SPARSE_HITS the walk form (a lean
-    // loop; measured +9 % at 1e-7) runs, above it the in-register count (+19 % at 3e-5).
+    // Which tensor-core count form (first estimate; the operand fill refines it from an
+    // occupancy histogram): the expected hits per pair of a set spread uniformly over its
+    // bounding box, (lattice points within the r2 ball) / (box sites), bounded above by
+    // the ball of radius sqrt(r2) + 1. Below TC_SPARSE_HITS the walk form (a lean loop;
+    // measured +9 % at 1e-7) runs, above it the in-register count (+19 % at 3e-5).
     // Either form gives the exact count; only the speed depends on the choice.
     {
         const double rad = sqrt(static_cast<double>(r2e)) + 1.0;
@@ -897,8 +899,9 @@ static bool use_tc(int64_t n, bool sum, bool allow_tc) {
     return allow_tc && n >= tc_min_n() && tc_enabled();
 }
 
-// Workspace layout: WsHeader | region | double partial[grid], where the region holds
-// either the extended record array or (tensor-core mode) the two operand arrays.
+// Workspace layout: WsHeader | region | double partial[slots] | uint32 hist[TC_HIST_CELLS],
+// where the region holds the extended record array or (tensor-core mode) the two operand
+// arrays, and the histogram is the integer tensor-core path's occupancy count.
 size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc) {
     if (n < 2) return sizeof(WsHeader);
     // the geometry depends only on the tile shape, which is the same for both classes
@@ -909,7 +912,7 @@ size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc) {
     if (use_tc(n, sum, allow_tc)) region = std::max(region, tc_region_bytes(n));
     region = (region + 255) & ~static_cast<size_t>(255);
     const size_t slots = static_cast<size_t>(std::max<int64_t>(g.grid, sm_count()));   // CTAs of either kernel
-    return sizeof(WsHeader) + region + slots * sizeof(double) + 256;
+    return sizeof(WsHeader) + region + slots * sizeof(double) + TC_HIST_CELLS * sizeof(uint32_t) + 256;
 }
 
 // Enqueues the whole single-set path on `stream` using workspace `ws` (>= single_ws_bytes).
@@ -932,6 +935,8 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     region_bytes = (region_bytes + 255) & ~static_cast<size_t>(255);
     Rec *E = reinterpret_cast<Rec *>(region);
     double *partial = reinterpret_cast<double *>(region + region_bytes);
+    const size_t slots = static_cast<size_t>(std::max<int64_t>(g.grid, sm_count()));   // as in single_ws_bytes
+    uint32_t *hist = reinterpret_cast<uint32_t *>(partial + slots);
     const int prep_threads = 256;
     const int64_t prep_blocks_full = (g.nrec + prep_threads - 1) / prep_threads;
     const int prep_blocks = static_cast<int>(std::min<int64_t>(prep_blocks_full, sm_count() * 8));
@@ -940,14 +945,14 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
         k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                  static_cast<const int32_t *>(p->y),
                                                  static_cast<const int32_t *>(p->z), n, r2, hdr,
-                                                 d_count, tc ? 1 : 0);
+                                                 d_count, tc ? 1 : 0, tc ? hist : nullptr);
         CC_CUDA(cudaGetLastError());
         k_fill_i32<<<prep_blocks, prep_threads, 0, stream>>>(
             static_cast<const int32_t *>(p->x), static_cast<const int32_t *>(p->y),
             static_cast<const int32_t *>(p->z), n, g.nrec, E, hdr);
         CC_CUDA(cudaGetLastError());
         if (tc) {
-            st = tc_enqueue_fill(p, n, region, hdr, stream);
+            st = tc_enqueue_fill(p, n, region, hdr, f32 ? nullptr : hist, stream);
             if (st != CC_OK) return st;
         }
     } else {
@@ -963,7 +968,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
             static_cast<const float *>(p->z), p->r, n, g.nrec, E, hdr);
         CC_CUDA(cudaGetLastError());
         if (tc) {
-            st = tc_enqueue_fill(p, n, region, hdr, stream);
+            st = tc_enqueue_fill(p, n, region, hdr, f32 ? nullptr : hist, stream);
             if (st != CC_OK) return st;
         }
     }
@@ -1021,7 +1026,8 @@ cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned 
         const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
         k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                  static_cast<const int32_t *>(p->y),
-                                                 static_cast<const int32_t *>(p->z), n, r2, hdr, d_count, 0);
+                                                 static_cast<const int32_t *>(p->z), n, r2, hdr, d_count, 0,
+                                                 nullptr);
         k_fill_i32<<<blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                static_cast<const int32_t *>(p->y),
                                                static_cast<const int32_t *>(p->z), n, nrec, E, hdr);
@@ -1065,7 +1071,7 @@ cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t
     const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
     k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                              static_cast<const int32_t *>(p->y),
-                                             static_cast<const int32_t *>(p->z), n, 0u, hdr, nullptr, 0);
+                                             static_cast<const int32_t *>(p->z), n, 0u, hdr, nullptr, 0, nullptr);
     CC_CUDA(cudaGetLastError());
     return CC_OK;
 }

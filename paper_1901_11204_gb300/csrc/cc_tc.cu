@@ -103,9 +103,17 @@ __device__ __forceinline__ int32_t tc_coord(const void *c, int64_t p, int axis, 
 template <bool F32>
 __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y, const void *__restrict__ z,
                           int64_t n, int64_t arows, int64_t elen, uint8_t *__restrict__ Aop,
-                          uint8_t *__restrict__ Bop, const WsHeader *__restrict__ h) {
-    if (h->mode != (F32 ? MODE_F32_TC : MODE_I32_TC)) return;
+                          uint8_t *__restrict__ Bop, WsHeader *__restrict__ h, uint32_t *__restrict__ hist) {
+    if (h->mode != (F32 ? MODE_F32_TC : MODE_I32_TC)) return;   // uniform over the grid
     const int32_t cx = h->cx, cy = h->cy, cz = h->cz;
+    // integer points: 16 cells per axis over the bounding box, for the occupancy histogram
+    int64_t box_lo[3] = {0, 0, 0}, box_n[3] = {1, 1, 1};   // minimum and span + 1 per axis
+    if (!F32 && hist) {
+        for (int a = 0; a < 3; ++a) {
+            box_lo[a] = ord_dec(h->umin[a]);
+            box_n[a] = static_cast<int64_t>(ord_dec(h->umax[a])) - box_lo[a] + 1;
+        }
+    }
     const int32_t off = h->ai_off;   // r2e + 1
     const int64_t rows = arows > elen ? arows : elen;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
@@ -117,6 +125,12 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
             if (r < n) {
                 const int32_t xi = tc_coord<F32>(x, r, 0, h) - cx, yi = tc_coord<F32>(y, r, 1, h) - cy,
                               zi = tc_coord<F32>(z, r, 2, h) - cz;
+                if (!F32 && hist && (r & (TC_HIST_STRIDE - 1)) == 0) {   // every 8th object
+                    const int64_t qx = (static_cast<int64_t>(xi) + cx - box_lo[0]) * 16 / box_n[0];
+                    const int64_t qy = (static_cast<int64_t>(yi) + cy - box_lo[1]) * 16 / box_n[1];
+                    const int64_t qz = (static_cast<int64_t>(zi) + cz - box_lo[2]) * 16 / box_n[2];
+                    atomicAdd(&hist[(qx * 16 + qy) * 16 + qz], 1u);
+                }
                 const int32_t c = xi * xi + yi * yi + zi * zi - off;
                 const int32_t cC = ((c + 1024) & 2047) - 1024;
                 const int32_t c1 = (c - cC) >> 11;   // exact: c - cC is a multiple of 2^11
@@ -145,6 +159,44 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
             *reinterpret_cast<float4 *>(gb + tc_off(r, 0)) = lo;
             *reinterpret_cast<float4 *>(gb + tc_off(r, 4)) = hi;
         }
+    }
+    if (F32 || !hist) return;
+    // The last block refines the count form from the histogram (of a systematic sample of
+    // one object in TC_HIST_STRIDE): pairs that share a cell,
+    // times the chance that a pair inside one cell is within reach (ball / cell sites),
+    // and never below the bounding-box estimate. Clustered sets, whose bounding box hides
+    // their density, then take the in-register form.
+    __shared__ bool last;
+    __shared__ double red[32];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&h->ticket0, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double same = 0.0;
+    for (int c = threadIdx.x; c < TC_HIST_CELLS; c += blockDim.x) {
+        const double k = static_cast<double>(__ldcg(&hist[c]));
+        same += 0.5 * k * (k - 1.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) same += __shfl_down_sync(0xFFFFFFFFu, same, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = same;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += red[w];
+        const double ns = static_cast<double>((n + TC_HIST_STRIDE - 1) / TC_HIST_STRIDE);   // sampled
+        const double pairs = 0.5 * ns * (ns - 1.0);
+        const double rad = sqrt(static_cast<double>(h->r2e)) + 1.0;
+        const double ball = 4.18879020478639 * rad * rad * rad;   // (4/3) pi rad^3
+        const double sites = static_cast<double>(box_n[0]) * static_cast<double>(box_n[1]) *
+                             static_cast<double>(box_n[2]);
+        const double cell_sites = sites / TC_HIST_CELLS;
+        const double est = fmax(ball / sites, (tot / pairs) * fmin(1.0, ball / cell_sites));
+        h->tc_form = est < TC_SPARSE_HITS ? 1 : 0;
+        h->ticket0 = 0;
     }
 }
 
@@ -760,7 +812,8 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
 // Enqueues the operand fill; it does nothing unless the preparation kernel chose
 // MODE_I32_TC (integer points) or MODE_F32_TC (spheres) for this call. `region` holds
 // tc_region_bytes(n).
-cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, cudaStream_t stream) {
+cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, uint32_t *hist,
+                          cudaStream_t stream) {
     TcLaunch L;
     cc_status st = tc_pick(L, false, false);   // every form has the same stage width
     if (st != CC_OK) return st;
@@ -769,10 +822,10 @@ cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHead
     const int blocks = static_cast<int>(std::min<int64_t>((rows + 255) / 256, static_cast<int64_t>(sm_count()) * 8));
     if (p->dtype == CC_F32) {
         k_fill_tc<true><<<blocks, 256, 0, stream>>>(p->x, p->y, p->z, n, g.M * TC_T, g.elen, region,
-                                                    region + g.a_bytes, hdr);
+                                                    region + g.a_bytes, hdr, nullptr);
     } else {
         k_fill_tc<false><<<blocks, 256, 0, stream>>>(p->x, p->y, p->z, n, g.M * TC_T, g.elen, region,
-                                                     region + g.a_bytes, hdr);
+                                                     region + g.a_bytes, hdr, hist);
     }
     CC_CUDA(cudaGetLastError());
     return CC_OK;

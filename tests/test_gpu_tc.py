@@ -212,6 +212,24 @@ def test_sums_all_points_identical(cc):
     assert abs(s - want) <= SUM_RTOL * want
 
 
+@pytest.mark.parametrize("frac", [0.0, 0.5, 0.95])
+def test_clustered_sets(cc, frac):
+    """A dense cluster inside a wide bounding box (the device then takes the in-register
+    count form; uniform sets take the walk form): exact either way."""
+    rng = np.random.default_rng(int(frac * 100) + 40)
+    n = 20001
+    x, y, z = box_points(rng, n, 1023)
+    k = int(frac * n)
+    for a in (x, y, z):
+        a[:k] = 500 + rng.integers(0, 24, k)
+    p = rng.permutation(n)
+    x, y, z = x[p], y[p], z[p]
+    got, mode = gpu_count(cc, x, y, z, 9)
+    assert mode == cc.MODE_TENSOR
+    assert got == oracle.count_i32(x, y, z, 9)
+    assert got == fp32_pipe_count(cc, x, y, z, 9)
+
+
 def test_tc_bounded_wait_timeout(cc):
     """No copy is issued: the MMA lane's wait runs out, every role stops, TMEM is freed,
     the status reads CC_ERR_TIMEOUT and the next call is correct."""
