@@ -125,6 +125,21 @@ def test_fall_backs(cc):
     check(cc, x, y, z, r, cc.MODE_FP32_SPHERES)
 
 
+def test_admission_boundary(cc):
+    """Largest span exactly 1 (S = 2046): the largest radius 0.010635799 gives r2q = 2048
+    (admitted), the next float 0.0106358 gives 2049 (FP32 pipe); exact either way."""
+    rng = np.random.default_rng(305)
+    n = 12000
+    x, y, z, r = spheres(rng, n, 0.002, 0.005)
+    x[0], y[0], z[0] = 0.0, 0.0, 0.0
+    x[1] = 1.0
+    for rmax, want in ((np.float32(0.010635799), cc.MODE_TENSOR_SPHERES),
+                       (np.float32(0.0106358), cc.MODE_FP32_SPHERES)):
+        r2 = r.copy()
+        r2[7] = rmax
+        check(cc, x, y, z, r2, want)
+
+
 def test_clustered_points(cc):
     """Half the points in a small cluster: many screened pairs, exact all the same."""
     rng = np.random.default_rng(304)
