@@ -153,6 +153,29 @@ def cfg2(n: int = 262144, same_cell: bool = False):
                 name=f"single set N={n} int32 [0,{box})^3 r2={r2}")
 
 
+def planted_positions(n: int) -> list[int]:
+    """Positions at which cfg2_planted places coincident objects: the first and last
+    objects, the middle of the set and its neighbours, and the objects around n/2 and
+    (n-1)/2 (for the proposed algorithm of Section 4 these pairs sit at both ends of an
+    object's window, across the wrap from the last object to the first, and on the even-N
+    extra step)."""
+    h = (n - 1) // 2
+    pos = {0, 1, h - 1, h, h + 1, n // 2 - 1, n // 2, n // 2 + 1, n - 2, n - 1, n // 3}
+    return sorted(p for p in pos if 0 <= p < n)
+
+
+def cfg2_planted(n: int = 262145):
+    """cfg2(n) with the objects at planted_positions(n) moved onto one lattice site, so
+    that every pair among them collides (all at squared distance 0 <= r2 = 9)."""
+    c = cfg2(n)
+    x, y, z = c["x"].copy(), c["y"].copy(), c["z"].copy()
+    pos = np.array(planted_positions(n), dtype=np.int64)
+    site = (511, 17, 1000)
+    x[pos], y[pos], z[pos] = site
+    return dict(x=x, y=y, z=z, r2=9,
+                name=f"single set N={n} int32 [0,1024)^3 r2=9 with {len(pos)} coincident objects planted")
+
+
 def cfg3(n: int = 131072):
     seed = SEED_BASE + 3
     x, y, z, r = sphere_points(n, seed)

@@ -29,6 +29,8 @@ def main():
         v = oracle.count_i32(s["x"], s["y"], s["z"], 0)
         assert v == oracle.count_colls(s["x"], s["y"], s["z"])   # Algorithm 1 cross-check
         rows.append((f"cfg2_samecell_n{n}_r2_0", v, ""))
+        p = synth.cfg2_planted(n)
+        rows.append((f"cfg2_planted_n{n}_r2_9", oracle.count_i32(p["x"], p["y"], p["z"], 9), ""))
     c = synth.cfg3()
     cnt, sm = oracle.count_f32(c["x"], c["y"], c["z"], c["r"])
     rows.append(("cfg3_n131072_f32", cnt, repr(sm)))

@@ -248,6 +248,52 @@ def pin_sets(o):
     assert np.array_equal(cnt, got)
 
 
+def pin_f32_sets_sums(o):
+    """Per-set FP32 counts and FP64 sums. (1) Every set is a permuted line of
+    unit-spaced spheres of radius 1.5 along its own axis: pairs collide iff |i-j| <= 3,
+    so set k of n objects has count sum_{m<=3} (n-m) and sum sum_{m<=3} (n-m)/m (the
+    standard algorithm of Section 4 applied to each set alone; Fractions give the exact
+    value). (2) On random sets each per-set sum equals the brute-force sum over all
+    ordered pairs of that slice (exact-rational predicate, math.fsum, halved)."""
+    rng = np.random.default_rng(15)
+    sizes = [0, 1, 2, 3, 4, 7, 50, 0, 101, 5]
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    cols = [[], [], []]
+    for k, n in enumerate(sizes):
+        axis = k % 3
+        for a in range(3):
+            cols[a].append(rng.permutation(n).astype(np.float32) if a == axis
+                           else np.full(n, 0.25 + k, dtype=np.float32))
+    x, y, z = (np.concatenate(c) if c else np.zeros(0, np.float32) for c in cols)
+    r = np.full(len(x), 1.5, dtype=np.float32)
+    cnt, sm = o.count_f32_sets(x, y, z, r, off)
+    for k, n in enumerate(sizes):
+        want = sum(n - m for m in range(1, min(3, n - 1) + 1))
+        wsum = sum(Fraction(n - m, m) for m in range(1, min(3, n - 1) + 1))
+        assert int(cnt[k]) == want, (k, n, int(cnt[k]), want)
+        assert abs(sm[k] - float(wsum)) <= 1e-12 * max(1.0, float(wsum)), (k, n, sm[k], wsum)
+    # random small sphere sets against all ordered pairs of each slice
+    sizes = [int(v) for v in rng.integers(0, 24, 6)]
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    m = int(off[-1])
+    x, y, z = (rng.random(m).astype(np.float32) * np.float32(0.04) for _ in range(3))
+    r = (0.002 + 0.01 * rng.random(m)).astype(np.float32)
+    cnt, sm = o.count_f32_sets(x, y, z, r, off)
+    for k in range(len(sizes)):
+        a, b = int(off[k]), int(off[k + 1])
+        terms = []
+        for i, j in itertools.permutations(range(a, b), 2):
+            if _spec_pred_exact((x[i], y[i], z[i], r[i]), (x[j], y[j], z[j], r[j])):
+                d = math.sqrt(sum((float(p[i]) - float(p[j])) ** 2 for p in (x, y, z)))
+                terms.append(1.0 / max(d, 1e-6))
+        assert len(terms) % 2 == 0
+        assert int(cnt[k]) == len(terms) // 2, (k, int(cnt[k]), len(terms))
+        want = math.fsum(terms) / 2
+        assert abs(sm[k] - want) <= 1e-12 * max(1.0, want), (k, sm[k], want)
+
+
 # ---- pins: FP32 spheres ---------------------------------------------------------------
 
 def pin_f32_line_closed_form(o):
@@ -459,6 +505,7 @@ ALL_PINS = [
     pin_same_site_algorithm1,
     pin_contacts_algorithm2,
     pin_sets,
+    pin_f32_sets_sums,
     pin_f32_line_closed_form,
     pin_f32_two_radii,
     pin_f32_ties_and_nan,

@@ -222,6 +222,30 @@ def test_cfg2_full_size(cc, n):
     assert gpu_count(cc, s["x"], s["y"], s["z"], 0) == oracle.count_colls(s["x"], s["y"], s["z"])
 
 
+@pytest.mark.parametrize("n", [262144, 262145])
+@pytest.mark.parametrize("tc", [True, False])
+def test_cfg2_planted_full_size(cc, n, tc):
+    """Headline sizes with coincident objects planted at the ends of the schedule's
+    windows: the last object against the first (across the wrap) and against the far end
+    of its window, the objects around (n-1)/2 and n/2 (the even-N extra step), on the
+    tensor-core kernel and on the FP32 pipe; the count must equal the oracle's golden."""
+    g = _golden()
+    p = synth.cfg2_planted(n)
+    key = f"cfg2_planted_n{n}_r2_9"
+    want = g[key][0] if key in g else oracle.count_i32(p["x"], p["y"], p["z"], 9)
+    cc.set_tensor_cores(tc)
+    try:
+        got = gpu_count(cc, p["x"], p["y"], p["z"], 9)
+        mode = cc.stream_mode()
+    finally:
+        cc.set_tensor_cores(True)
+    assert mode == (cc.MODE_TENSOR if tc else cc.MODE_FP32_EXACT)
+    assert got == want
+    # the planted pairs alone: every pair among the planted objects collides
+    k = len(synth.planted_positions(n))
+    assert want >= k * (k - 1) // 2
+
+
 def test_cfg3_full_size(cc):
     g = _golden()
     c = synth.cfg3()

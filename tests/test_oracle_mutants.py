@@ -62,6 +62,11 @@ MUTANTS = {
     "i32_sum_strict": ("if (d2 <= (int64_t)r2) {\n                double d", "if (d2 < (int64_t)r2) {\n                double d"),
     "i32_sum_dropped_dy": ("int64_t d2 = dx * dx + dy * dy + dz * dz;\n            if (d2 <= (int64_t)r2) {\n                double d",
                            "int64_t d2 = dx * dx + dz * dz;\n            if (d2 <= (int64_t)r2) {\n                double d"),
+    "sets_sum_halved": ("if (sums) sums[k] = s;", "if (sums) sums[k] = s / 2;"),
+    "sets_sum_wrong_partner": ("                    s += term_f64(x[i], y[i], z[i], x[j], y[j], z[j]);\n                }\n        counts[k] = c;",
+                               "                    s += term_f64(x[i], y[i], z[i], x[a], y[a], z[a]);\n                }\n        counts[k] = c;"),
+    "sets_sum_not_reset": ("        uint64_t c = 0;\n        double s = 0.0;\n        for (int64_t i = a; i < b; ++i)",
+                           "        uint64_t c = 0;\n        static double s = 0.0;\n        for (int64_t i = a; i < b; ++i)"),
     "work_formula": ("return (n - 1) / 2 + ((n % 2 == 0 && i < n / 2) ? 1 : 0);",
                      "return n / 2;"),
 }
