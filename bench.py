@@ -446,8 +446,9 @@ def main():
         "issue_roofline": issue_roofline_line,
         "e2e": e2e,
         # per count: reset, min/max + mode, record fill, operand fill, the two tensor-core
-        # count forms and the FP32-pipe kernel (the kernels and fill not chosen return at once)
-        "gpu_launches": (7 if tensor else 4) * len(sets) * args.steps,
+        # count forms, the FP32-pipe kernel (the kernels and fill not chosen return at
+        # once) and the finalisation kernel
+        "gpu_launches": (8 if tensor else 5) * len(sets) * args.steps,
         "pair_kernel_modes": modes,
         "clocks": clocks,
         "wall_s_timed_region": wall,
@@ -457,6 +458,7 @@ def main():
     if rank == 0 and not args.no_extras:
         line["fp32_pipe_step"] = bench_fp32_pipe_step(cc, torch, step, outs, want, tests_per_step,
                                                       roofline_peak_int(sms, fmax) / 1e9, flush)
+        line["config1"] = bench_config1(cc, torch, dev, sms, fmax)
         line["f32_spheres"] = bench_f32(cc, torch, dev, sms, fmax, peak_src, peaks)
         line["i32_sums"] = bench_i32_sums(cc, torch, dev)
         line["batched"] = bench_batched(cc, torch, dev)
@@ -517,6 +519,71 @@ def _time(fn, reps, torch, stream=None):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def _golden_counts():
+    out = {}
+    path = os.path.join(ROOT, "tests", "golden", "full_size_counts.txt")
+    if os.path.exists(path):
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = int(v)
+    return out
+
+
+def bench_config1(cc, torch, dev, sms, fmax, calls=2000):
+    """Config 1 (N = 4096 int32 points in [0,64)^3, r2 = 16: one small, latency-bound
+    set): the one-launch small-set kernel. Device time per call over back-to-back calls
+    (CUDA events), host-observed latency of one call with its synchronisation, the kernel's
+    own event-timed duration, and the CPU oracle on the same set; the count must equal the
+    oracle's golden value."""
+    import oracle
+    c = synth.cfg1()
+    n = len(c["x"])
+    t = [torch.from_numpy(c[k]).to(dev) for k in ("x", "y", "z")]
+    out = torch.empty(1, dtype=torch.int64, device=dev)
+    cc.count_pairs(*t, r2=c["r2"], out=out)
+    torch.cuda.synchronize()
+    got = cc.as_u64(out)
+    want = _golden_counts().get("cfg1_n4096_r2_16")
+    if want is None:
+        want = oracle.count_i32(c["x"], c["y"], c["z"], c["r2"])
+    assert got == want, (got, want)
+    mode = cc.stream_mode()
+    ms = _time(lambda: cc.count_pairs(*t, r2=c["r2"], out=out), calls, torch)
+    cc.profile_enable(True)
+    cc.profile_read()
+    for _ in range(200):
+        cc.count_pairs(*t, r2=c["r2"], out=out)
+    torch.cuda.synchronize()
+    kern_ms, kern_n = cc.profile_read()
+    cc.profile_enable(False)
+    lat = []
+    for _ in range(500):
+        a = time.perf_counter()
+        cc.count_pairs(*t, r2=c["r2"], out=out)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - a)
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 0.5:
+        oracle.count_i32(c["x"], c["y"], c["z"], c["r2"])
+        reps += 1
+    cpu_s = (time.perf_counter() - t0) / reps
+    oracle.set_threads(0)
+    tests = pairs(n)
+    return {"workload": c["name"], "count": got, "count_equals_golden": True, "mode": mode,
+            "kernel": "k_small (one launch per call)", "launches_per_call": 1,
+            "us_per_call": ms * 1e3, "gpairs_s": tests / (ms * 1e-3) / 1e9,
+            "kernel_us": kern_ms / max(kern_n, 1) * 1e3,
+            "kernel_gpairs_s": tests / (kern_ms / max(kern_n, 1) * 1e-3) / 1e9 if kern_ms > 0 else None,
+            "host_latency_p50_us": float(np.percentile(lat, 50) * 1e6),
+            "host_latency_p99_us": float(np.percentile(lat, 99) * 1e6),
+            "cpu_oracle_one_core_us": cpu_s * 1e6, "cpu_oracle_gpairs_s": tests / cpu_s / 1e9,
+            "issue_roofline_peak": issue_roofline(sms, fmax, 8),
+            "note": "latency-bound: 8.4e6 pair tests per call; the roofline fraction is not meaningful"}
 
 
 def bench_f32(cc, torch, dev, sms, fmax, peak_src, peaks):
@@ -665,27 +732,41 @@ def bench_batched(cc, torch, dev):
     items = plan.last_items()
     n = np.diff(off)
     tests = int((n * (n - 1) // 2).sum())
-    # plain per-set launches on the same GPU: a sample of consecutive sets, extrapolated
-    sample = 5000
-    outs = torch.empty(sample, dtype=torch.int64, device=dev)
-    xs = [(int(off[k]), int(off[k + 1])) for k in range(sample)]
+    # plain per-set launches on the same GPU, every set: cc_count_pairs per set, which for
+    # sets below 8192 objects is one launch of the small-set kernel (the same stage loop,
+    # no preparation pass), and the tensor-core path for the one set of 8192
+    outs = torch.empty(S, dtype=torch.int64, device=dev)
+    xs = [(int(off[k]), int(off[k + 1])) for k in range(S)]
+    views = [(t[0][a:b], t[1][a:b], t[2][a:b]) for (a, b) in xs]
+    out_views = [outs[k:k + 1] for k in range(S)]
+    r2 = c["r2"]
 
     def plain():
-        for k, (a, b) in enumerate(xs):
-            cc.count_pairs(t[0][a:b], t[1][a:b], t[2][a:b], r2=c["r2"], out=outs[k:k + 1])
+        for v, o in zip(views, out_views):
+            cc.count_pairs(*v, r2=r2, out=o)
 
-    ms_plain = _time(plain, 1, torch)
-    ok = bool((outs == holder["c"][:sample]).all().item())
+    plain()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    e0.record()
+    plain()
+    e1.record()
+    torch.cuda.synchronize()
+    wall_plain = time.perf_counter() - w0
+    ms_plain = e0.elapsed_time(e1)
+    ok = bool((outs == holder["c"]).all().item())
     plan.close()
-    per_set_plain_us = ms_plain / sample * 1e3
     return {"workload": f"{S} pruned sets, {int(off[-1])} int32 points, r2={c['r2']}",
             "tile_table": "autotuned (paper_1901_11204_gb300/tune_gb300.json)" if tune else "built-in defaults",
             "ms": ms, "sets_per_s": S / (ms * 1e-3), "gpairs_s": tests / (ms * 1e-3) / 1e9,
             "work_items": items, "pair_tests": tests,
-            "plain_us_per_set": per_set_plain_us,
-            "plain_ms_extrapolated": per_set_plain_us * S / 1e3,
-            "speedup_vs_plain": per_set_plain_us * S / 1e3 / ms,
-            "plain_sample_sets": sample, "plain_matches_batched": ok}
+            "plain_ms": ms_plain, "plain_wall_s": wall_plain, "plain_us_per_set": ms_plain / S * 1e3,
+            "plain_launches_per_set": 1,
+            "speedup_vs_plain": ms_plain / ms,
+            "plain_sets": S, "plain_matches_batched": ok,
+            "plain_note": "one cc_count_pairs call per set over all sets, device time between events "
+                          "bracketing the whole loop (host enqueue rate included)"}
 
 
 def bench_serving(cc, torch, dev, nq):
@@ -720,11 +801,37 @@ def bench_serving(cc, torch, dev, nq):
         lat.append(time.perf_counter() - a)
     serial_rate = probe / (time.perf_counter() - t0)
 
-    def run_stream(rate):
-        q = synth.cfg5_queries(nq, len(pool), rate)
+    def serial_stream(rate, count):
+        """Serial plain launches under the same Poisson arrivals: each request waits for
+        its arrival time and for the previous request, then runs synchronously; latency is
+        completion minus arrival (the queueing a one-at-a-time service sees)."""
+        q = synth.cfg5_queries(count, len(pool), rate)
+        lat_s = []
+        start = time.perf_counter()
+        for k in range(count):
+            target = start + q["t"][k]
+            while time.perf_counter() < target:
+                pass
+            s = dsets[int(q["set_id"][k])]
+            if len(s) == 3:
+                cc.count_pairs(*s, r2=9)
+            elif q["op"][k] == 2:
+                cc.interaction_sum(s[0], s[1], s[2], r=s[3])
+            else:
+                cc.count_pairs(s[0], s[1], s[2], r=s[3])
+            torch.cuda.synchronize()
+            lat_s.append(time.perf_counter() - target)
+        end = time.perf_counter()
+        lat_s = np.array(lat_s)
+        return {"offered_qps": rate, "queries": count, "achieved_qps": count / (end - start),
+                "p50_ms": float(np.percentile(lat_s, 50) * 1e3), "p99_ms": float(np.percentile(lat_s, 99) * 1e3)}
+
+    def run_stream(rate, count=None):
+        count = nq if count is None else count
+        q = synth.cfg5_queries(count, len(pool), rate)
         start = time.perf_counter()
         t = q["t"]
-        for k in range(nq):
+        for k in range(count):
             target = start + t[k]
             while True:
                 d = target - time.perf_counter()
@@ -752,6 +859,15 @@ def bench_serving(cc, torch, dev, nq):
     runs = [sat]
     for frac in (0.5, 0.8):
         runs.append(run_stream(frac * sat["achieved_qps"]))
+    # served against serial plain launches at equal offered rates: half the serial
+    # capacity (both keep up), the serial capacity, and a tenth of the served saturation
+    low = min(nq, 10000)
+    equal_rate = []
+    for label, rate in (("0.5x serial capacity", 0.5 * serial_rate), ("serial capacity", serial_rate),
+                        ("0.1x served saturation", 0.1 * sat["achieved_qps"])):
+        served = run_stream(rate, low)
+        plain = serial_stream(rate, min(low, 4000))
+        equal_rate.append({"label": label, "offered_qps": rate, "served": served, "serial_plain": plain})
     st = srv.stats()
     resident = st["peak_bytes"]
     srv.close()
@@ -787,7 +903,7 @@ def bench_serving(cc, torch, dev, nq):
             "serial_plain_qps": serial_rate,
             "serial_plain_p50_ms": float(np.percentile(lat, 50) * 1e3),
             "serial_plain_p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "runs": runs, "server_stats": st,
+            "runs": runs, "equal_rate": equal_rate, "server_stats": st,
             "speedup_vs_serial": sat["achieved_qps"] / serial_rate}
 
 

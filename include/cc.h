@@ -21,8 +21,9 @@
  * Errors. Argument errors are detected on the host before anything is enqueued and
  *   return CC_ERR_INVALID_ARG. Launch errors return CC_ERR_CUDA. Conditions that only
  *   the device can see (integer span beyond the supported range, a bounded wait that
- *   ran out) are recorded in a device status word of the stream's workspace: the output
- *   count is then set to CC_COUNT_INVALID, and cc_stream_status() returns the code.
+ *   ran out) are recorded in a device status word of the stream's workspace: the call's
+ *   output count is then set to CC_COUNT_INVALID (its sum, if any, to NaN) by the call's
+ *   last kernel, and cc_stream_status() returns the code.
  *   cc_last_error() gives a message for the last failing call of the calling thread.
  * Workspace. The single-set calls keep one scratch buffer per stream, grown on demand
  *   with stream-ordered allocation (cudaMallocAsync) on that stream. The first call on
@@ -130,7 +131,9 @@ cc_status cc_stream_status(void *stream);
 /* Diagnostic: synchronises `stream` and writes to *mode which pair kernel the device
  * chose for the last cc_count_pairs / cc_interaction_sum call on it:
  *   CC_MODE_FP32_EXACT   integer points, expanded-square form exact in FP32 (FP32 pipe)
- *   CC_MODE_INT_WIDE     integer points, int32 difference form (spans up to 32767)
+ *   CC_MODE_INT_WIDE     integer points, int32 difference form (spans up to 32767);
+ *                        for sets below 8192 objects (one launch, each unit of work
+ *                        centred on its own objects) some units needed this form
  *   CC_MODE_RANGE_ERROR  span above 32767: nothing was counted
  *   CC_MODE_FP32_SPHERES FP32 spheres
  *   CC_MODE_TENSOR       integer points, the same exact form as a TF32 tensor-core
@@ -166,13 +169,15 @@ cc_status cc_set_tensor_cores(int32_t enable);
  * allocation. The paper has no counterpart; this is a deployment variant of the
  * single-set path. Scratch is one static device array of 8 MiB inside the library,
  * held by every GPU that loads the library until the process exits; it fits sets of
- * about 340 thousand objects, and larger n is rejected with CC_ERR_INVALID_ARG and a
+ * about 349 thousand objects, and larger n is rejected with CC_ERR_INVALID_ARG and a
  * message that states the exact limit. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) for that device; make that first call before
  * any stream capture. All calls share the one array, so calls that overlap on the GPU
  * (for example on two streams) race and give wrong counts; serialise them. Each call
  * clears the state it needs. The count is CC_COUNT_INVALID when the device rejects the
- * integer range. Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+ * integer range or a bounded wait runs out; this call has no stream workspace, so
+ * cc_stream_status() does not report it: the count is the only report. Allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library call. */
 cc_status cc_count_pairs_noalloc(const cc_points *p, int64_t n, uint32_t r2,
                                  unsigned long long *d_count, void *stream);
 
@@ -219,8 +224,14 @@ typedef struct {
 
 /* Creates a server with a device-memory budget for resident sets plus per-batch scratch
  * and at most max_slots requests admitted (in flight) at once. It owns two streams and
- * one scheduler thread. */
+ * one scheduler thread; its batching plans use the built-in tile table. */
 cc_status cc_server_create(cc_server **srv, size_t mem_budget_bytes, int32_t max_slots);
+
+/* The same, with the batching plans built from tune_table_json (the autotuner's JSON, as
+ * for cc_plan_create; NULL = built-in defaults). CC_ERR_INVALID_ARG for a malformed
+ * table. */
+cc_status cc_server_create_tuned(cc_server **srv, size_t mem_budget_bytes, int32_t max_slots,
+                                 const char *tune_table_json);
 
 /* Copies a set into device memory (host or device source pointers, detected) and
  * registers it; its id goes to *set_id. Fails with CC_ERR_NOMEM beyond the budget. */
@@ -234,7 +245,10 @@ cc_status cc_server_unregister_set(cc_server *srv, int32_t set_id);
 cc_status cc_server_submit(cc_server *srv, int32_t set_id, int32_t op, uint32_t r2,
                            uint64_t req_id);
 
-/* Moves up to max finished results to out[]; *n_out receives how many. */
+/* Moves up to max finished results to out[]; *n_out receives how many. A result's status
+ * is CC_OK, or the device-detected condition of its request (CC_ERR_RANGE: integer span
+ * beyond the supported range; CC_ERR_TIMEOUT: a bounded wait ran out), with the count
+ * CC_COUNT_INVALID and the sum NaN; CC_ERR_CUDA when its batch could not be launched. */
 cc_status cc_server_poll(cc_server *srv, cc_result *out, int32_t max, int32_t *n_out);
 
 /* Blocks until every submitted request has finished or timeout_s passed. */

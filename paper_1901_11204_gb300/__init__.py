@@ -77,6 +77,7 @@ _SIGS = {
     "cc_count_pairs_batched": ([_VP, _PTS, _VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP], ctypes.c_int),
     "cc_plan_last_items": ([_VP, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cc_server_create": ([ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int32], ctypes.c_int),
+    "cc_server_create_tuned": ([ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int32, ctypes.c_char_p], ctypes.c_int),
     "cc_server_register_set": ([_VP, _PTS, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "cc_server_unregister_set": ([_VP, ctypes.c_int32], ctypes.c_int),
     "cc_server_submit": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64], ctypes.c_int),
@@ -342,12 +343,27 @@ class Plan:
 
 # ---- serving ---------------------------------------------------------------------------
 
-class Server:
-    """Continuous-batching server (cc_server) over device-resident sets."""
+TUNE_TABLE_PATH = os.path.join(_HERE, "tune_gb300.json")
 
-    def __init__(self, mem_budget_bytes: int, max_slots: int):
+
+def default_tune_table() -> str | None:
+    """The band table the autotuner measured on GB300 (tune_gb300.json), or None."""
+    if os.path.exists(TUNE_TABLE_PATH):
+        with open(TUNE_TABLE_PATH) as f:
+            return f.read()
+    return None
+
+
+class Server:
+    """Continuous-batching server (cc_server) over device-resident sets. Its batching
+    plans use tune_table_json (default: the packaged GB300 table; None: built-in)."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int, tune_table_json: str | None = "default"):
         h = ctypes.c_void_p()
-        _check(lib().cc_server_create(ctypes.byref(h), int(mem_budget_bytes), int(max_slots)))
+        if tune_table_json == "default":
+            tune_table_json = default_tune_table()
+        js = tune_table_json.encode() if tune_table_json else None
+        _check(lib().cc_server_create_tuned(ctypes.byref(h), int(mem_budget_bytes), int(max_slots), js))
         self.handle = h.value
         self._keep = []
 

@@ -311,71 +311,6 @@ __global__ void k_b_emit(const BatchParams *__restrict__ P, const int32_t *cnt, 
 
 // ---- the per-item pair loop -------------------------------------------------------------
 
-// Loads the R objects of this lane for the tile starting at tile0 from the set's raw
-// arrays (same register conventions as the single-set kernel).
-template <int R>
-__device__ __forceinline__ void load_i_raw(IState<R> &s, const SetDesc &d, const SetAux &x, int32_t tile0,
-                                           int lane) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int32_t i = tile0 + lane + 32 * r;
-        const bool valid = i < d.n;
-        const int32_t ii = valid ? i : 0;
-        if (x.mode == MODE_I32_FAST) {
-            const int32_t xi = static_cast<const int32_t *>(d.x)[ii] - x.cx;
-            const int32_t yi = static_cast<const int32_t *>(d.y)[ii] - x.cy;
-            const int32_t zi = static_cast<const int32_t *>(d.z)[ii] - x.cz;
-            s.a[r] = f2_dup(-2.0f * static_cast<float>(xi));
-            s.b[r] = f2_dup(-2.0f * static_cast<float>(yi));
-            s.c[r] = f2_dup(-2.0f * static_cast<float>(zi));
-            s.d[r] = f2_dup(valid ? static_cast<float>(xi * xi + yi * yi + zi * zi - x.ai_off)
-                                  : __int_as_float(0x7f800000));
-        } else if (x.mode == MODE_F32) {
-            const float xi = static_cast<const float *>(d.x)[ii];
-            s.a[r] = f2_dup(valid ? xi : __int_as_float(0x7fc00000));
-            s.b[r] = f2_dup(static_cast<const float *>(d.y)[ii]);
-            s.c[r] = f2_dup(static_cast<const float *>(d.z)[ii]);
-            s.d[r] = f2_dup(d.r[ii]);
-        } else {
-            s.a[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.x)[ii]));
-            s.b[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.y)[ii]));
-            s.c[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.z)[ii]));
-            s.d[r] = 0;
-        }
-    }
-}
-
-// Stages the extended objects [e0, e0 + kJSB) of the set into the warp's slot as 32
-// pair-interleaved records (lane l writes record l: objects e0+2l, e0+2l+1, mod n).
-__device__ __forceinline__ void stage_load(Rec *slot, const SetDesc &d, const SetAux &x, int32_t e0, int lane) {
-    Rec rec;
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-        const int32_t e = e0 + 2 * lane + l;
-        const int32_t p = e < d.n ? e : e % static_cast<int32_t>(d.n);
-        if (x.mode == MODE_I32_FAST) {
-            const int32_t xi = static_cast<const int32_t *>(d.x)[p] - x.cx;
-            const int32_t yi = static_cast<const int32_t *>(d.y)[p] - x.cy;
-            const int32_t zi = static_cast<const int32_t *>(d.z)[p] - x.cz;
-            rec.x[l] = static_cast<float>(xi);
-            rec.y[l] = static_cast<float>(yi);
-            rec.z[l] = static_cast<float>(zi);
-            rec.w[l] = static_cast<float>(xi * xi + yi * yi + zi * zi);
-        } else if (x.mode == MODE_F32) {
-            rec.x[l] = static_cast<const float *>(d.x)[p];
-            rec.y[l] = static_cast<const float *>(d.y)[p];
-            rec.z[l] = static_cast<const float *>(d.z)[p];
-            rec.w[l] = d.r[p];
-        } else {
-            rec.x[l] = __int_as_float(static_cast<const int32_t *>(d.x)[p]);
-            rec.y[l] = __int_as_float(static_cast<const int32_t *>(d.y)[p]);
-            rec.z[l] = __int_as_float(static_cast<const int32_t *>(d.z)[p]);
-            rec.w[l] = 0.0f;
-        }
-    }
-    slot[lane] = rec;
-}
-
 template <int MODE, int R, bool SUM>
 __device__ void run_item(const SetDesc &d, const SetAux &x, const Band &b, int32_t local, Rec *slot,
                          unsigned long long &cnt_out, double &sum_out) {
@@ -390,8 +325,9 @@ __device__ void run_item(const SetDesc &d, const SetAux &x, const Band &b, int32
     const int32_t k0 = b.sc > 0 ? chunk * b.sc : 0;
     const int32_t k1 = b.sc > 0 ? min(k0 + b.sc, K) : K;
     const int32_t tile0 = tile * T;
+    const RawSet rs{d.x, d.y, d.z, d.r, n, x.cx, x.cy, x.cz, x.ai_off};
     IState<R> s;
-    load_i_raw<R>(s, d, x, tile0, lane);
+    load_i_raw<MODE, R>(s, rs, tile0, lane);
     const uint32_t r2 = MODE == MODE_F32 ? 0u : x.r2e;
     const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(slot);
     unsigned long long cnt = 0;
@@ -399,7 +335,7 @@ __device__ void run_item(const SetDesc &d, const SetAux &x, const Band &b, int32
     for (int32_t k = k0; k < k1; ++k) {
         const int32_t eo0 = k * kJSB;
         __syncwarp();
-        stage_load(slot, d, x, tile0 + eo0, lane);
+        stage_load_raw<MODE>(slot, rs, tile0 + eo0, lane);
         __syncwarp();
         const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (eo0 + kJSB - 1 <= h);
         cnt += full_stage ? stage_run<MODE, 32, R, kJSB, false, SUM>(s, st, eo0, lane, tile0, n, h, r2, sum)
@@ -691,22 +627,10 @@ struct cc_plan {
     std::mutex mu;
 };
 
-// k_b_main instance: CC_BMAIN_MINB (1..4) for sweeps, else the measured best.
-static const void *main_kernel() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("CC_BMAIN_MINB");
-        v = e ? atoi(e) : 0;
-    }
-    // measured on config 4 (100k small sets): 1 -> 0.57 ms, 2 -> 0.40, 3 -> 0.38, 4 -> 0.38
-    // (4 spills heavily in the wide bands; 3 is the default)
-    switch (v) {
-        case 1: return reinterpret_cast<const void *>(k_b_main<1>);
-        case 2: return reinterpret_cast<const void *>(k_b_main<2>);
-        case 4: return reinterpret_cast<const void *>(k_b_main<4>);
-        default: return reinterpret_cast<const void *>(k_b_main<3>);
-    }
-}
+// k_b_main instance: registers capped for 3 resident CTAs per SM. Measured on config 4
+// (100k small sets) with 1, 2, 3 and 4 CTAs per SM: 0.57, 0.40, 0.38 and 0.38 ms (4 spills
+// heavily in the wide bands).
+static const void *main_kernel() { return reinterpret_cast<const void *>(k_b_main<3>); }
 
 static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
     const int sms = sm_count();

@@ -78,7 +78,11 @@ struct WsHeader {
     double qscale;        // ... quantisation scale, 2046 / the largest per-axis span
     int32_t tc_form;      // integer tensor-core count: 0 = count blocks in registers,
                           // 1 = walk the (rare) blocks with a hit (sparse hits expected)
-    uint32_t pad[9];
+    uint32_t cstatus;     // ST_* bits of the current call only (cleared by each call's
+                          // reset); a non-zero value invalidates the call's outputs
+    uint32_t sbox[7];     // small-set kernel: per-axis ~min and max codes of the set, and a
+                          // flag for units that took the wide form (0 between calls)
+    uint32_t sticket;     // small-set kernel: last-CTA ticket (0 between calls)
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 static_assert(int{MODE_I32_FAST} == int{CC_MODE_FP32_EXACT} && int{MODE_I32_WIDE} == int{CC_MODE_INT_WIDE} &&
@@ -288,6 +292,13 @@ __device__ __forceinline__ uint32_t ord_enc_f(float f) {
 }
 __device__ __forceinline__ float ord_dec_f(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// Records a device-detected condition (ST_* bits) for the current call and for
+// cc_stream_status(): the call's outputs are invalidated by its finalisation.
+__device__ __forceinline__ void flag_status(WsHeader *h, uint32_t bits) {
+    atomicOr(&h->status, bits);
+    atomicOr(&h->cstatus, bits);
 }
 
 #endif  // __CUDACC__

@@ -26,7 +26,8 @@ size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc);
 cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
                          float *d_sum, void *ws, cudaStream_t stream, bool allow_tc);
 
-// 8 MiB of scratch: enough for sets of about 340 thousand objects.
+// 8 MiB of scratch: enough for sets of about 349 thousand objects (the extended record
+// array of 32 bytes per pair of objects, per-CTA slots and the header).
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -54,18 +55,19 @@ static cc_status noalloc_scratch(void **out) {
     return CC_OK;
 }
 
-// Largest set size whose workspace fits in the scratch array.
+// Largest set size whose workspace fits in the scratch array (computed once; function-
+// local static initialisation is thread-safe).
 static int64_t noalloc_max_n() {
-    static int64_t cached = -1;
-    if (cached >= 0) return cached;
-    int64_t lo = 1, hi = int64_t(1) << 26;
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo + 1) / 2;
-        const size_t b = single_ws_bytes(mid, false, false);
-        if (b != 0 && b <= kNoAllocScratchBytes) lo = mid;
-        else hi = mid - 1;
-    }
-    cached = lo;
+    static const int64_t cached = []() {
+        int64_t lo = 1, hi = int64_t(1) << 26;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo + 1) / 2;
+            const size_t b = single_ws_bytes(mid, false, false);
+            if (b != 0 && b <= kNoAllocScratchBytes) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    }();
     return cached;
 }
 
@@ -93,10 +95,12 @@ cc_status cc_count_pairs_noalloc(const cc_points *p, int64_t n, uint32_t r2, uns
     cc_status st = noalloc_scratch(&ws);
     if (st != CC_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the header's status word keeps the previous call's bits: start each call from zero
+    // The header's status word keeps the previous call's bits: start each call from zero.
+    // A condition the device detects for this call (integer span beyond the range, a
+    // bounded wait that ran out) makes the call's last kernel write CC_COUNT_INVALID.
     CC_CUDA(cudaMemsetAsync(&reinterpret_cast<WsHeader *>(ws)->status, 0, sizeof(uint32_t), s));
     // the tensor-core operands would need about three times the scratch: the static
-    // array serves the FP32-pipe kernel only
+    // array serves the FP32-pipe kernels only
     return single_enqueue(p, n, r2, d_count, nullptr, ws, s, false);
 }
 

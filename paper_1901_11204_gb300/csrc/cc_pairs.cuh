@@ -132,6 +132,83 @@ __device__ __noinline__ double pair_terms(f2 a, f2 b, f2 c, f2 d, ulonglong2 p0,
     return sum;
 }
 
+// ---- staging straight from the caller's SoA arrays (batched kernel) ----------------------
+
+// A set as the caller holds it, with the integer centre and offset of the fast form.
+struct RawSet {
+    const void *x, *y, *z;
+    const float *r;
+    int32_t n;
+    int32_t cx, cy, cz;   // integer centre subtracted before the FP32 conversion
+    int32_t ai_off;       // r2e + 1 (fast integer form)
+};
+
+// Loads the R objects of this lane for the warp tile starting at tile0 (objects
+// tile0 + lane + 32 r) in the register form of MODE. Objects past n get a state that
+// never hits (fast form, spheres) or no evaluations (wide form: evals_of is 0).
+template <int MODE, int R>
+__device__ __forceinline__ void load_i_raw(IState<R> &s, const RawSet &d, int32_t tile0, int lane) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int32_t i = tile0 + lane + 32 * r;
+        const bool valid = i < d.n;
+        const int32_t ii = valid ? i : 0;
+        if (MODE == MODE_I32_FAST) {
+            const int32_t xi = static_cast<const int32_t *>(d.x)[ii] - d.cx;
+            const int32_t yi = static_cast<const int32_t *>(d.y)[ii] - d.cy;
+            const int32_t zi = static_cast<const int32_t *>(d.z)[ii] - d.cz;
+            s.a[r] = f2_dup(-2.0f * static_cast<float>(xi));
+            s.b[r] = f2_dup(-2.0f * static_cast<float>(yi));
+            s.c[r] = f2_dup(-2.0f * static_cast<float>(zi));
+            s.d[r] = f2_dup(valid ? static_cast<float>(xi * xi + yi * yi + zi * zi - d.ai_off)
+                                  : __int_as_float(0x7f800000));   // +inf: never hits
+        } else if (MODE == MODE_F32) {
+            const float xi = static_cast<const float *>(d.x)[ii];
+            s.a[r] = f2_dup(valid ? xi : __int_as_float(0x7fc00000));   // NaN: never hits
+            s.b[r] = f2_dup(static_cast<const float *>(d.y)[ii]);
+            s.c[r] = f2_dup(static_cast<const float *>(d.z)[ii]);
+            s.d[r] = f2_dup(d.r[ii]);
+        } else {
+            s.a[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.x)[ii]));
+            s.b[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.y)[ii]));
+            s.c[r] = f2_dup(__int_as_float(static_cast<const int32_t *>(d.z)[ii]));
+            s.d[r] = 0;
+        }
+    }
+}
+
+// Stages the extended objects [e0, e0 + 64) of the set (indices mod n) into a warp's
+// slot as 32 pair-interleaved records: lane l writes record l (objects e0+2l, e0+2l+1).
+template <int MODE>
+__device__ __forceinline__ void stage_load_raw(Rec *slot, const RawSet &d, int32_t e0, int lane) {
+    Rec rec;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int32_t e = e0 + 2 * lane + l;
+        const int32_t p = e < d.n ? e : e % d.n;
+        if (MODE == MODE_I32_FAST) {
+            const int32_t xi = static_cast<const int32_t *>(d.x)[p] - d.cx;
+            const int32_t yi = static_cast<const int32_t *>(d.y)[p] - d.cy;
+            const int32_t zi = static_cast<const int32_t *>(d.z)[p] - d.cz;
+            rec.x[l] = static_cast<float>(xi);
+            rec.y[l] = static_cast<float>(yi);
+            rec.z[l] = static_cast<float>(zi);
+            rec.w[l] = static_cast<float>(xi * xi + yi * yi + zi * zi);
+        } else if (MODE == MODE_F32) {
+            rec.x[l] = static_cast<const float *>(d.x)[p];
+            rec.y[l] = static_cast<const float *>(d.y)[p];
+            rec.z[l] = static_cast<const float *>(d.z)[p];
+            rec.w[l] = d.r[p];
+        } else {
+            rec.x[l] = __int_as_float(static_cast<const int32_t *>(d.x)[p]);
+            rec.y[l] = __int_as_float(static_cast<const int32_t *>(d.y)[p]);
+            rec.z[l] = __int_as_float(static_cast<const int32_t *>(d.z)[p]);
+            rec.w[l] = 0.0f;
+        }
+    }
+    slot[lane] = rec;
+}
+
 // One stage for one consumer thread: JS staged objects against the thread's R objects.
 // MASKED applies the cyclic schedule's validity per pair: s = e - i must be in 1..evals(i).
 // With SUM, record pairs that produced a hit are re-walked for their interaction terms.

@@ -83,6 +83,8 @@ struct Lane {
     float *h_sums = nullptr;                 // pinned
     cudaEvent_t done = nullptr;
     std::vector<Req> batch;
+    std::vector<int32_t> singles;            // batch entries served by the single-set path
+    cc_status fail_status = CC_OK;           // the batch could not be enqueued
     bool busy = false;
     size_t scratch = 0;
 };
@@ -129,9 +131,24 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
+// Moves a finished batch's results to the done queue. A count of CC_COUNT_INVALID marks a
+// device-detected error: on the batched path a set beyond the integer range; on the
+// single-set route whichever condition the lane stream's status word recorded (a bounded
+// wait that ran out, or the range), read here, off the lock, only when such a count
+// appears.
 static void harvest(cc_server *S, Lane &L) {
     NvtxRange range("cc_server harvest");
     const double t = now_s();
+    cc_status single_err = CC_OK;
+    for (int32_t k : L.singles) {
+        if (L.h_counts[k] == CC_COUNT_INVALID) {
+            single_err = cc_stream_status(L.stream);
+            if (single_err == CC_OK) single_err = CC_ERR_RANGE;
+            break;
+        }
+    }
+    std::vector<char> is_single(L.batch.size(), 0);
+    for (int32_t k : L.singles) is_single[k] = 1;
     std::lock_guard<std::mutex> lk(S->mu);
     for (size_t k = 0; k < L.batch.size(); ++k) {
         const Req &q = L.batch[k];
@@ -140,7 +157,9 @@ static void harvest(cc_server *S, Lane &L) {
         r.set_id = q.set_id;
         r.op = q.op;
         const unsigned long long c = L.h_counts[k];
-        r.status = c == CC_COUNT_INVALID ? CC_ERR_RANGE : CC_OK;
+        r.status = L.fail_status != CC_OK ? L.fail_status
+                   : c != CC_COUNT_INVALID ? CC_OK
+                   : (is_single[k] ? single_err : CC_ERR_RANGE);
         r.count = c;
         r.sum = q.op == CC_OP_SUM ? L.h_sums[k] : 0.0f;
         r.t_arrive_s = q.t_arrive;
@@ -152,17 +171,25 @@ static void harvest(cc_server *S, Lane &L) {
     S->inflight_bytes -= L.scratch;
     S->finished += static_cast<int64_t>(L.batch.size());
     L.batch.clear();
+    L.singles.clear();
+    L.fail_status = CC_OK;
     L.scratch = 0;
     L.busy = false;
     S->cv.notify_all();
 }
 
-// Forms and launches one batch on lane L (called with S->mu NOT held).
+// Forms one batch on lane L under S->mu (admission, descriptors), then enqueues its copies,
+// graph launch and single-set calls with the lock released, so that client submit() and
+// poll() never wait for CUDA calls. Only the scheduler thread touches L, and an admitted
+// request holds a reference on its set, so the set's buffers stay valid meanwhile.
 static bool launch(cc_server *S, Lane &L) {
     NvtxRange range("cc_server form+launch batch");
     std::vector<Req> batch;
+    std::vector<cc_points> single_pts;   // points of the single-set entries (same order as L.singles)
+    std::vector<int64_t> single_n;
     size_t scratch = 0;
     int64_t points = 0;
+    bool any_sum = false;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         while (!S->pending.empty()) {
@@ -184,8 +211,7 @@ static bool launch(cc_server *S, Lane &L) {
         S->batches += 1;
         S->peak_inflight = std::max(S->peak_inflight, S->inflight);
         S->peak_bytes = std::max<int64_t>(S->peak_bytes, static_cast<int64_t>(S->resident_bytes + S->inflight_bytes));
-        bool any_sum = false;
-        std::vector<int32_t> singles;   // batch entries served by the single-set path
+        L.singles.clear();
         for (size_t k = 0; k < batch.size(); ++k) {
             const SetRec &sr = S->sets[batch[k].set_id];
             SetDescHost d;
@@ -198,50 +224,51 @@ static bool launch(cc_server *S, Lane &L) {
             d.dtype = sr.dtype;
             d.r2 = batch[k].r2;
             if (sr.single) {
+                cc_points pts;
+                pts.dtype = sr.dtype;
+                pts.x = d.x;
+                pts.y = d.y;
+                pts.z = d.z;
+                pts.r = d.r;
+                single_pts.push_back(pts);
+                single_n.push_back(sr.n);
                 d.n = 0;   // the batch writes 0; the single-set call below writes the result
-                singles.push_back(static_cast<int32_t>(k));
+                L.singles.push_back(static_cast<int32_t>(k));
             }
             L.h_sets[k] = d;
             any_sum = any_sum || batch[k].op == CC_OP_SUM;
         }
-        L.batch = std::move(batch);
-        L.scratch = scratch;
-        L.busy = true;
-        const int32_t nb = static_cast<int32_t>(L.batch.size());
-        cudaError_t e = cudaMemcpyAsync(plan_sets_buffer_v(L.plan), L.h_sets, sizeof(SetDescHost) * nb,
-                                        cudaMemcpyHostToDevice, L.stream);
-        cc_status st = e == cudaSuccess
-                           ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
-                           : CC_ERR_CUDA;
-        // queries on large sets: one single-set call each, stream-ordered after the
-        // batch (this thread is the lane stream's only user, so its workspace is too)
-        for (size_t j = 0; st == CC_OK && j < singles.size(); ++j) {
-            const int32_t k = singles[j];
-            const SetRec &sr = S->sets[L.batch[k].set_id];
-            const size_t col = static_cast<size_t>(sr.n) * 4;
-            cc_points pts;
-            pts.dtype = sr.dtype;
-            pts.x = sr.buf;
-            pts.y = static_cast<char *>(sr.buf) + col;
-            pts.z = static_cast<char *>(sr.buf) + 2 * col;
-            pts.r = sr.dtype == CC_F32 ? reinterpret_cast<const float *>(static_cast<char *>(sr.buf) + 3 * col)
-                                       : nullptr;
-            st = L.batch[k].op == CC_OP_SUM
-                     ? cc_interaction_sum(&pts, sr.n, L.batch[k].r2, L.d_sums + k, L.d_counts + k, L.stream)
-                     : cc_count_pairs(&pts, sr.n, L.batch[k].r2, L.d_counts + k, L.stream);
-            S->single_launches += 1;
-        }
-        if (st == CC_OK) e = cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(unsigned long long) * nb,
-                                             cudaMemcpyDeviceToHost, L.stream);
-        if (st == CC_OK && e == cudaSuccess && any_sum)
-            e = cudaMemcpyAsync(L.h_sums, L.d_sums, sizeof(float) * nb, cudaMemcpyDeviceToHost, L.stream);
-        if (st == CC_OK && e == cudaSuccess) e = cudaEventRecord(L.done, L.stream);
-        if (st != CC_OK || e != cudaSuccess) {
-            S->sched_error = std::string("batch launch failed: ") + cudaGetErrorString(e) + " " + cc_last_error();
-            for (size_t k = 0; k < L.batch.size(); ++k) L.h_counts[k] = CC_COUNT_INVALID;
-            cudaStreamSynchronize(L.stream);
-            cudaEventRecord(L.done, L.stream);
-        }
+        S->single_launches += static_cast<int64_t>(L.singles.size());
+    }
+    L.batch = std::move(batch);
+    L.scratch = scratch;
+    L.busy = true;
+    const int32_t nb = static_cast<int32_t>(L.batch.size());
+    cudaError_t e = cudaMemcpyAsync(plan_sets_buffer_v(L.plan), L.h_sets, sizeof(SetDescHost) * nb,
+                                    cudaMemcpyHostToDevice, L.stream);
+    cc_status st = e == cudaSuccess ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
+                                    : CC_ERR_CUDA;
+    // queries on large sets: one single-set call each, stream-ordered after the batch
+    // (this thread is the lane stream's only user, so its workspace is too)
+    for (size_t j = 0; st == CC_OK && j < L.singles.size(); ++j) {
+        const int32_t k = L.singles[j];
+        st = L.batch[k].op == CC_OP_SUM
+                 ? cc_interaction_sum(&single_pts[j], single_n[j], L.batch[k].r2, L.d_sums + k, L.d_counts + k, L.stream)
+                 : cc_count_pairs(&single_pts[j], single_n[j], L.batch[k].r2, L.d_counts + k, L.stream);
+    }
+    if (st == CC_OK) e = cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(unsigned long long) * nb,
+                                         cudaMemcpyDeviceToHost, L.stream);
+    if (st == CC_OK && e == cudaSuccess && any_sum)
+        e = cudaMemcpyAsync(L.h_sums, L.d_sums, sizeof(float) * nb, cudaMemcpyDeviceToHost, L.stream);
+    if (st == CC_OK && e == cudaSuccess) e = cudaEventRecord(L.done, L.stream);
+    if (st != CC_OK || e != cudaSuccess) {
+        const std::string msg = std::string("batch launch failed: ") + cudaGetErrorString(e) + " " + cc_last_error();
+        cudaStreamSynchronize(L.stream);
+        for (size_t k = 0; k < L.batch.size(); ++k) L.h_counts[k] = CC_COUNT_INVALID;
+        L.fail_status = st != CC_OK ? st : CC_ERR_CUDA;   // every entry of this batch reports it
+        cudaEventRecord(L.done, L.stream);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->sched_error = msg;
     }
     return true;
 }
@@ -276,6 +303,11 @@ static void scheduler(cc_server *S) {
 extern "C" {
 
 cc_status cc_server_create(cc_server **srv, size_t mem_budget_bytes, int32_t max_slots) {
+    return cc_server_create_tuned(srv, mem_budget_bytes, max_slots, nullptr);
+}
+
+cc_status cc_server_create_tuned(cc_server **srv, size_t mem_budget_bytes, int32_t max_slots,
+                                 const char *tune_table_json) {
     if (!srv) return fail(CC_ERR_INVALID_ARG, "srv is NULL");
     *srv = nullptr;
     if (max_slots <= 0 || max_slots > 65536) return fail(CC_ERR_INVALID_ARG, "max_slots must be in 1..65536");
@@ -296,7 +328,7 @@ cc_status cc_server_create(cc_server **srv, size_t mem_budget_bytes, int32_t max
             cc_server_destroy(S);
             return fail(CC_ERR_NOMEM, std::string("server allocation: ") + cudaGetErrorString(e));
         }
-        cc_status st = cc_plan_create(&L.plan, nullptr, max_slots, kPlanMaxPoints);
+        cc_status st = cc_plan_create(&L.plan, tune_table_json, max_slots, kPlanMaxPoints);
         if (st != CC_OK) {
             cc_server_destroy(S);
             return st;

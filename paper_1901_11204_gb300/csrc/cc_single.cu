@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <utility>
 
 #include "cc_internal.cuh"
 #include "cc_pairs.cuh"
@@ -42,15 +43,15 @@ cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHead
                           cudaStream_t stream);
 cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region, WsHeader *hdr,
                            unsigned long long *d_count, float *d_sum, double *partial, cudaStream_t stream);
-// Smallest set for which counts and sums take a tensor-core form: 8192 objects (the
-// measured crossover: at 8192 both forms take about 33 us per call, at 12288 the tensor
-// cores 25-30 % less), or the environment variable CC_TC_MIN_N (read once).
+// Smallest set for which counts and sums take a tensor-core form (and below which they
+// take the one-launch small-set kernel): 8192 objects (the measured crossover between the
+// tensor-core and FP32-pipe forms: at 8192 both take about 33 us per call, at 12288 the
+// tensor cores 25-30 % less), or the environment variable CC_TC_MIN_N (read once).
 int64_t tc_min_n() {
-    static int64_t v = -1;
-    if (v < 0) {
+    static const int64_t v = []() {
         const char *e = getenv("CC_TC_MIN_N");
-        v = (e && atoll(e) >= 2) ? static_cast<int64_t>(atoll(e)) : 8192;
-    }
+        return (e && atoll(e) >= 2) ? static_cast<int64_t>(atoll(e)) : int64_t{8192};
+    }();
     return v;
 }
 
@@ -71,8 +72,20 @@ __global__ void k_reset(WsHeader *h, int32_t mode, unsigned long long *d_count, 
         h->ticket1 = 0;
         h->qbad = 0u;
         h->qrmax = 0u;
+        h->cstatus = 0u;
         if (d_count) *d_count = 0ull;
         if (d_sum) *d_sum = 0.0f;
+    }
+}
+
+// Last kernel of every single-set call: when the device detected a condition for this
+// call (a bounded wait that ran out, an integer span beyond the supported range), the
+// partial results the pair kernels may have added are replaced by the invalid markers:
+// CC_COUNT_INVALID for the count and a quiet NaN for the sum.
+__global__ void k_finalize(const WsHeader *h, unsigned long long *d_count, float *d_sum) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && h->cstatus != 0u) {
+        if (d_count) *d_count = CC_COUNT_INVALID;
+        if (d_sum) *d_sum = __int_as_float(0x7fc00000);
     }
 }
 
@@ -132,7 +145,7 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
     int32_t mode;
     if (!range_ok) {
         mode = MODE_RANGE_ERR;
-        atomicOr(&h->status, ST_RANGE);
+        flag_status(h, ST_RANGE);
         if (d_count) *d_count = CC_COUNT_INVALID;
     } else if (m <= FAST_MAX_HALF_SPAN) {
         mode = MODE_I32_FAST;
@@ -373,163 +386,6 @@ __device__ __forceinline__ void load_i(IState<R> &s, const PairArgs &A, int32_t 
     }
 }
 
-template <int NT, int R, int JS, int NS>
-struct SmemLayout {
-    static constexpr int kStageBytes = JS * 16;
-    static constexpr int kStages = NS * kStageBytes;
-    static constexpr int kBars = 2 * NS * 8;
-    static constexpr int kRed = (NT / 32 + 1) * 16;
-    static constexpr int kTotal = kStages + kBars + kRed + 16;
-};
-
-template <int MODE, int NT, int R, int JS, int NS, bool SUM>
-__device__ __forceinline__ void consumer_loop(const PairArgs &A, uint8_t *smem, uint64_t *full,
-                                              uint64_t *empty, volatile int *abort_flag,
-                                              int64_t u0, int64_t u1, int tid,
-                                              unsigned long long &cnt64, double &sum) {
-    constexpr int T = NT * R;
-    const int32_t ai_off = A.hdr->ai_off;
-    const uint32_t r2 = A.hdr->r2e;
-    IState<R> s;
-    int64_t cur_tile = -1;
-    const int lane = tid & 31;
-    int64_t q = 0;
-    for (int64_t u = u0; u < u1; ++u, ++q) {
-        const int64_t t = u / A.K;
-        const int32_t k = static_cast<int32_t>(u - t * A.K);
-        if (t != cur_tile) {
-            load_i<NT, R>(s, A, MODE, t * T, tid, ai_off);
-            cur_tile = t;
-        }
-        const int slot = static_cast<int>(q % NS);
-        const uint32_t par = static_cast<uint32_t>((q / NS) & 1);
-        if (!mbar_wait_bounded(&full[slot], par, A.wait_ns, abort_flag)) {
-            if (!*abort_flag) atomicOr(&A.hdr->status, ST_TIMEOUT);
-            *abort_flag = 1;
-            break;
-        }
-        const ulonglong2 *st =
-            reinterpret_cast<const ulonglong2 *>(smem + slot * SmemLayout<NT, R, JS, NS>::kStageBytes);
-        const int32_t eo0 = k * JS;  // offset of the stage's first object from the tile start
-        const bool full_stage = (MODE != MODE_I32_WIDE) && (eo0 >= T) && (eo0 + JS - 1 <= A.h);
-        const uint32_t c =
-            full_stage ? stage_run<MODE, NT, R, JS, false, SUM>(s, st, eo0, tid, t * T, A.n, A.h, r2, sum)
-                       : stage_run<MODE, NT, R, JS, true, SUM>(s, st, eo0, tid, t * T, A.n, A.h, r2, sum);
-        cnt64 += c;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
-    }
-}
-
-template <int CLASS, int NT, int R, int JS, int NS, bool SUM, int MINB>
-__global__ void __launch_bounds__(NT + 32, MINB) k_pairs(PairArgs A) {
-    using L = SmemLayout<NT, R, JS, NS>;
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kStages);
-    uint64_t *empty = full + NS;
-    unsigned long long *red_cnt = reinterpret_cast<unsigned long long *>(smem + L::kStages + L::kBars);
-    double *red_sum = reinterpret_cast<double *>(red_cnt + (NT / 32 + 1));
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kStages + L::kBars + L::kRed);
-
-    const int tid = threadIdx.x;
-    const int warp = tid / 32;
-    const int32_t hmode = A.hdr->mode;
-    const int32_t mode = CLASS == CLASS_F32 ? MODE_F32 : hmode;
-    // invalid, or one of the tensor-core forms runs this call
-    if (mode == MODE_RANGE_ERR || mode == MODE_I32_TC || hmode == MODE_F32_TC) return;
-
-    if (tid == 0) {
-        for (int i = 0; i < NS; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], NT / 32);
-        }
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    const int64_t G = gridDim.x;
-    const int64_t u0 = (A.units * static_cast<int64_t>(blockIdx.x)) / G;
-    const int64_t u1 = (A.units * static_cast<int64_t>(blockIdx.x + 1)) / G;
-    constexpr int T = NT * R;
-
-    unsigned long long cnt64 = 0;
-    double sum = 0.0;
-
-    if (warp == NT / 32) {
-        // producer warp: one elected lane issues the bulk copies
-        if ((tid & 31) == 0) {
-            int64_t q = 0;
-            for (int64_t u = u0; u < u1; ++u, ++q) {
-                const int slot = static_cast<int>(q % NS);
-                if (q >= NS) {
-                    const uint32_t par = static_cast<uint32_t>(((q / NS) - 1) & 1);
-                    if (!mbar_wait_bounded(&empty[slot], par, A.wait_ns, abort_flag)) {
-                        if (!*abort_flag) atomicOr(&A.hdr->status, ST_TIMEOUT);
-                        *abort_flag = 1;
-                        break;
-                    }
-                }
-                if (A.stall) continue;   // test hook: nothing is copied, consumers time out
-                const int64_t t = u / A.K;
-                const int64_t k = u - t * A.K;
-                const int64_t e0 = t * T + k * JS;   // even: T and JS are even
-                mbar_arrive_expect_tx(&full[slot], L::kStageBytes);
-                bulk_g2s(smem + slot * L::kStageBytes, A.E + (e0 >> 1), L::kStageBytes, &full[slot]);
-            }
-            // before leaving, make sure no copy this CTA issued is still in flight
-            if (!A.stall) {
-                const int64_t issued = q;
-                for (int64_t qq = (issued > NS ? issued - NS : 0); qq < issued; ++qq) {
-                    const int slot = static_cast<int>(qq % NS);
-                    (void)mbar_wait_bounded(&full[slot], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
-                }
-            }
-        }
-    } else if (CLASS == CLASS_F32) {
-        consumer_loop<MODE_F32, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
-    } else if (mode == MODE_I32_FAST) {
-        consumer_loop<MODE_I32_FAST, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
-    } else {
-        consumer_loop<MODE_I32_WIDE, NT, R, JS, NS, SUM>(A, smem, full, empty, abort_flag, u0, u1, tid, cnt64, sum);
-    }
-
-    // ---- reduction: warp shuffle -> shared memory -> one 64-bit atomic per CTA --------
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cnt64 += __shfl_down_sync(0xFFFFFFFFu, cnt64, o);
-        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
-    }
-    if ((tid & 31) == 0) {
-        red_cnt[warp] = cnt64;
-        if (SUM) red_sum[warp] = sum;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long c = 0;
-        double sm = 0.0;
-        for (int w = 0; w < NT / 32 + 1; ++w) {
-            c += red_cnt[w];
-            if (SUM) sm += red_sum[w];
-        }
-        if (c && A.d_count) atomicAdd(A.d_count, c);
-        if (SUM) {
-            // fixed-order final reduction by the last CTA (ticket, no waiting)
-            A.partial[blockIdx.x] = sm;
-            __threadfence();
-            const unsigned ticket = atomicAdd(&A.hdr->ticket1, 1u);
-            if (ticket == gridDim.x - 1) {
-                __threadfence();
-                double tot = 0.0;
-                for (unsigned b = 0; b < gridDim.x; ++b)
-                    tot += *reinterpret_cast<volatile double *>(&A.partial[b]);
-                *A.d_sum = static_cast<float>(tot);
-                A.hdr->ticket1 = 0;
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------------------
 // warp-independent variant: every warp owns its i-tile (32*R objects) and its own
 // NS-deep ring of j-stages, refilled by its own lane 0 with cp.async.bulk. Warps never
@@ -581,7 +437,7 @@ __device__ __forceinline__ void warp_loop(const PairArgs &A, uint8_t *ring, uint
         }
         const int slot = static_cast<int>(q % NS);
         if (!mbar_wait_bounded(&full[slot], static_cast<uint32_t>((q / NS) & 1), A.wait_ns)) {
-            if (lane == 0) atomicOr(&A.hdr->status, ST_TIMEOUT);
+            if (lane == 0) flag_status(A.hdr, ST_TIMEOUT);
             timed_out = true;
             break;
         }
@@ -719,7 +575,7 @@ __device__ __forceinline__ void straight_loop(const PairArgs &A, uint8_t *ring, 
     for (; k < K; ++k) {
         const int slot = static_cast<int>(k % NS);
         if (!mbar_wait_bounded(&full[slot], static_cast<uint32_t>((k / NS) & 1), A.wait_ns)) {
-            if (lane == 0) atomicOr(&A.hdr->status, ST_TIMEOUT);
+            if (lane == 0) flag_status(A.hdr, ST_TIMEOUT);
             timed_out = true;
             break;
         }
@@ -779,93 +635,362 @@ __global__ void __launch_bounds__(NW * 32, 1) k_pairs_straight(PairArgs A) {
 // host side
 // ---------------------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------------------
+// small sets (n below the tensor-core threshold): one launch, no preparation pass
+// ---------------------------------------------------------------------------------------
+// Warp tiles of 32*R objects and j-stages of 64 objects staged by each warp from the
+// caller's arrays into its own shared-memory slot; a unit is (tile, stage) and every warp
+// takes an equal contiguous share of the units (the balance of the proposed algorithm,
+// Section 4). Instead of a set-wide min/max pass, each unit centres its objects on the
+// midpoint of their own bounding box: the fast form (exact FP32, see FAST_MAX_HALF_SPAN)
+// runs when that box's half-span is within the bound, the integer difference form
+// otherwise. The set-wide span (range precondition) is reduced from the tile objects
+// while the units run; per-CTA partials go to slots that the last CTA to finish adds in
+// CTA order, then it writes the count (or CC_COUNT_INVALID) and the sum, and resets the
+// header words it used.
+
+constexpr int SMALL_WARPS = 8;   // warps per CTA
+constexpr int SMALL_JS = 64;     // objects per j-stage
+// r2 as compared by the fast form: every pair it evaluates has d^2 <= 12 * 1182^2, so
+// clamping r2 there keeps n_i - r2e - 1 exact in FP32 without changing any decision.
+constexpr uint32_t SMALL_R2E_MAX = 12u * FAST_MAX_HALF_SPAN * FAST_MAX_HALF_SPAN;
+
+struct SmallArgs {
+    const void *x, *y, *z;
+    const float *r;
+    int32_t n, h, K;             // objects, (n-1)/2, stages per tile
+    int32_t units;
+    uint32_t r2;
+    WsHeader *hdr;
+    unsigned long long *slot_cnt;   // one per CTA
+    double *slot_sum;               // one per CTA (sums only)
+    unsigned long long *d_count;
+    float *d_sum;
+};
+
+template <int R>
+struct TileRaw {
+    int32_t x[R], y[R], z[R];   // raw integer coordinates of the lane's tile objects
+};
+
+// Integer units: load the stage, centre it and the tile on the unit's bounding box and
+// run the fast form, or the wide form when the box is too wide for it.
+template <int R, bool SUM>
+__device__ __forceinline__ uint32_t small_unit_i32(const SmallArgs &A, const TileRaw<R> &tr, int32_t tile0,
+                                                   int32_t k, Rec *slot, int lane, double &sum, bool &wide) {
+    constexpr int T = 32 * R;
+    const int32_t eo0 = k * SMALL_JS;
+    const int32_t *X = static_cast<const int32_t *>(A.x);
+    const int32_t *Y = static_cast<const int32_t *>(A.y);
+    const int32_t *Z = static_cast<const int32_t *>(A.z);
+    int32_t sx[2], sy[2], sz[2];
+    uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int32_t e = tile0 + eo0 + 2 * lane + l;
+        const int32_t p = e < A.n ? e : e % A.n;
+        sx[l] = X[p];
+        sy[l] = Y[p];
+        sz[l] = Z[p];
+        mn[0] = min(mn[0], ord_enc(sx[l]));
+        mx[0] = max(mx[0], ord_enc(sx[l]));
+        mn[1] = min(mn[1], ord_enc(sy[l]));
+        mx[1] = max(mx[1], ord_enc(sy[l]));
+        mn[2] = min(mn[2], ord_enc(sz[l]));
+        mx[2] = max(mx[2], ord_enc(sz[l]));
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        // objects past n repeat the tile's first object (their evaluations are masked)
+        mn[0] = min(mn[0], ord_enc(tr.x[r]));
+        mx[0] = max(mx[0], ord_enc(tr.x[r]));
+        mn[1] = min(mn[1], ord_enc(tr.y[r]));
+        mx[1] = max(mx[1], ord_enc(tr.y[r]));
+        mn[2] = min(mn[2], ord_enc(tr.z[r]));
+        mx[2] = max(mx[2], ord_enc(tr.z[r]));
+    }
+    int32_t c[3];
+    int64_t m = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t lo = ord_dec(__reduce_min_sync(0xFFFFFFFFu, mn[a]));
+        const int64_t hi = ord_dec(__reduce_max_sync(0xFFFFFFFFu, mx[a]));
+        c[a] = static_cast<int32_t>(lo + (hi - lo) / 2);
+        m = max(m, (hi - lo + 1) / 2);
+    }
+    const bool full = eo0 >= T && eo0 + SMALL_JS - 1 <= A.h;
+    __syncwarp();   // every lane is done reading the slot's previous stage
+    if (m <= FAST_MAX_HALF_SPAN) {
+        const uint32_t r2e = A.r2 < SMALL_R2E_MAX ? A.r2 : SMALL_R2E_MAX;
+        const int32_t ai_off = static_cast<int32_t>(r2e) + 1;
+        Rec rec;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int32_t xi = sx[l] - c[0], yi = sy[l] - c[1], zi = sz[l] - c[2];
+            rec.x[l] = static_cast<float>(xi);
+            rec.y[l] = static_cast<float>(yi);
+            rec.z[l] = static_cast<float>(zi);
+            rec.w[l] = static_cast<float>(xi * xi + yi * yi + zi * zi);
+        }
+        slot[lane] = rec;
+        IState<R> s;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const bool valid = tile0 + lane + 32 * r < A.n;
+            const int32_t xi = tr.x[r] - c[0], yi = tr.y[r] - c[1], zi = tr.z[r] - c[2];
+            s.a[r] = f2_dup(-2.0f * static_cast<float>(xi));
+            s.b[r] = f2_dup(-2.0f * static_cast<float>(yi));
+            s.c[r] = f2_dup(-2.0f * static_cast<float>(zi));
+            s.d[r] = f2_dup(valid ? static_cast<float>(xi * xi + yi * yi + zi * zi - ai_off)
+                                  : __int_as_float(0x7f800000));   // +inf: never hits
+        }
+        __syncwarp();
+        const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(slot);
+        return full ? stage_run<MODE_I32_FAST, 32, R, SMALL_JS, false, SUM>(s, st, eo0, lane, tile0, A.n, A.h, r2e,
+                                                                            sum)
+                    : stage_run<MODE_I32_FAST, 32, R, SMALL_JS, true, SUM>(s, st, eo0, lane, tile0, A.n, A.h, r2e,
+                                                                           sum);
+    }
+    wide = true;
+    Rec rec;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        rec.x[l] = __int_as_float(sx[l]);
+        rec.y[l] = __int_as_float(sy[l]);
+        rec.z[l] = __int_as_float(sz[l]);
+        rec.w[l] = 0.0f;
+    }
+    slot[lane] = rec;
+    IState<R> s;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        s.a[r] = f2_dup(__int_as_float(tr.x[r]));
+        s.b[r] = f2_dup(__int_as_float(tr.y[r]));
+        s.c[r] = f2_dup(__int_as_float(tr.z[r]));
+        s.d[r] = 0;
+    }
+    __syncwarp();
+    const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(slot);
+    return stage_run<MODE_I32_WIDE, 32, R, SMALL_JS, true, SUM>(s, st, eo0, lane, tile0, A.n, A.h, A.r2, sum);
+}
+
+template <bool F32, int R, bool SUM>
+__global__ void __launch_bounds__(SMALL_WARPS * 32, 2) k_small(SmallArgs A) {
+    constexpr int T = 32 * R;
+    __shared__ Rec slots[SMALL_WARPS][SMALL_JS / 2];
+    __shared__ unsigned long long red_cnt[SMALL_WARPS];
+    __shared__ double red_sum[SMALL_WARPS];
+    __shared__ uint32_t red_box[SMALL_WARPS][7];
+    __shared__ bool last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Rec *slot = slots[warp];
+    const int64_t W = static_cast<int64_t>(gridDim.x) * SMALL_WARPS;
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * SMALL_WARPS + warp;
+    const int32_t u0 = static_cast<int32_t>((A.units * w) / W);
+    const int32_t u1 = static_cast<int32_t>((A.units * (w + 1)) / W);
+    uint32_t cnt = 0;
+    unsigned long long cnt64 = 0;
+    double sum = 0.0;
+    bool wide = false;
+    // set-wide bounding box of the tile objects (range precondition), order-preserving codes
+    uint32_t bmn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, bmx[3] = {0u, 0u, 0u};
+    int32_t cur = -1;
+    TileRaw<R> tr;
+    IState<R> fs;   // spheres: the tile's register state
+    const RawSet rs{A.x, A.y, A.z, A.r, A.n, 0, 0, 0, 0};
+    for (int32_t u = u0; u < u1; ++u) {
+        const int32_t t = u / A.K;
+        const int32_t k = u - t * A.K;
+        const int32_t tile0 = t * T;
+        if (t != cur) {
+            cur = t;
+            if constexpr (F32) {
+                load_i_raw<MODE_F32, R>(fs, rs, tile0, lane);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int32_t i = tile0 + lane + 32 * r;
+                    const int32_t ii = i < A.n ? i : tile0;   // past n: a valid object, masked
+                    tr.x[r] = static_cast<const int32_t *>(A.x)[ii];
+                    tr.y[r] = static_cast<const int32_t *>(A.y)[ii];
+                    tr.z[r] = static_cast<const int32_t *>(A.z)[ii];
+                    bmn[0] = min(bmn[0], ord_enc(tr.x[r]));
+                    bmx[0] = max(bmx[0], ord_enc(tr.x[r]));
+                    bmn[1] = min(bmn[1], ord_enc(tr.y[r]));
+                    bmx[1] = max(bmx[1], ord_enc(tr.y[r]));
+                    bmn[2] = min(bmn[2], ord_enc(tr.z[r]));
+                    bmx[2] = max(bmx[2], ord_enc(tr.z[r]));
+                }
+            }
+        }
+        if constexpr (F32) {
+            const int32_t eo0 = k * SMALL_JS;
+            __syncwarp();
+            stage_load_raw<MODE_F32>(slot, rs, tile0 + eo0, lane);
+            __syncwarp();
+            const ulonglong2 *st = reinterpret_cast<const ulonglong2 *>(slot);
+            const bool full = eo0 >= T && eo0 + SMALL_JS - 1 <= A.h;
+            cnt += full ? stage_run<MODE_F32, 32, R, SMALL_JS, false, SUM>(fs, st, eo0, lane, tile0, A.n, A.h, 0u,
+                                                                           sum)
+                        : stage_run<MODE_F32, 32, R, SMALL_JS, true, SUM>(fs, st, eo0, lane, tile0, A.n, A.h, 0u,
+                                                                          sum);
+        } else {
+            cnt += small_unit_i32<R, SUM>(A, tr, tile0, k, slot, lane, sum, wide);
+        }
+        if (((u - u0) & 1023) == 1023) {   // keep the per-lane counter far from overflow
+            cnt64 += cnt;
+            cnt = 0;
+        }
+    }
+    cnt64 += cnt;
+    // ---- per CTA: counts, sums, box, wide flag -------------------------------------------
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt64 += __shfl_down_sync(0xFFFFFFFFu, cnt64, o);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    }
+    if (!F32) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bmn[a] = __reduce_min_sync(0xFFFFFFFFu, bmn[a]);
+            bmx[a] = __reduce_max_sync(0xFFFFFFFFu, bmx[a]);
+        }
+    }
+    const uint32_t wide_any = __any_sync(0xFFFFFFFFu, wide) ? 1u : 0u;
+    if (lane == 0) {
+        red_cnt[warp] = cnt64;
+        red_sum[warp] = sum;
+        for (int a = 0; a < 3; ++a) {
+            red_box[warp][a] = ~bmn[a];   // merged with max, like the maximum
+            red_box[warp][3 + a] = bmx[a];
+        }
+        red_box[warp][6] = wide_any;
+    }
+    __syncthreads();
+    WsHeader *h = A.hdr;
+    if (threadIdx.x == 0) {
+        unsigned long long c = 0;
+        double sm = 0.0;
+        uint32_t box[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        for (int i = 0; i < SMALL_WARPS; ++i) {
+            c += red_cnt[i];
+            sm += red_sum[i];
+            for (int j = 0; j < 7; ++j) box[j] = max(box[j], red_box[i][j]);
+        }
+        A.slot_cnt[blockIdx.x] = c;
+        if (SUM) A.slot_sum[blockIdx.x] = sm;
+        if (!F32) {
+            for (int j = 0; j < 6; ++j)
+                if (box[j]) atomicMax(&h->sbox[j], box[j]);
+            if (box[6]) atomicOr(&h->sbox[6], 1u);
+        }
+        __threadfence();
+        last = atomicAdd(&h->sticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    unsigned long long tot = 0;
+    double stot = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+        tot += *reinterpret_cast<volatile unsigned long long *>(&A.slot_cnt[b]);
+        if (SUM) stot += *reinterpret_cast<volatile double *>(&A.slot_sum[b]);
+    }
+    int32_t mode = MODE_F32;
+    if (!F32) {
+        bool range_ok = true;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t lo = ord_dec(~atomicAdd(&h->sbox[a], 0u));
+            const int64_t hi = ord_dec(atomicAdd(&h->sbox[3 + a], 0u));
+            if (hi - lo > WIDE_MAX_SPAN) range_ok = false;
+        }
+        mode = !range_ok ? MODE_RANGE_ERR : (atomicAdd(&h->sbox[6], 0u) ? MODE_I32_WIDE : MODE_I32_FAST);
+        for (int j = 0; j < 7; ++j) h->sbox[j] = 0u;
+        if (!range_ok) flag_status(h, ST_RANGE);
+    }
+    h->mode = mode;
+    h->sticket = 0u;
+    if (A.d_count) *A.d_count = mode == MODE_RANGE_ERR ? CC_COUNT_INVALID : tot;
+    if (SUM) *A.d_sum = mode == MODE_RANGE_ERR ? __int_as_float(0x7fc00000) : static_cast<float>(stot);
+}
+
+struct SmallLaunch {
+    const void *fn;
+    int R;
+};
+
+template <bool F32, int R, bool SUM>
+static SmallLaunch small_launch_of() {
+    return SmallLaunch{reinterpret_cast<const void *>(k_small<F32, R, SUM>), R};
+}
+
+// Objects per lane of the small-set kernel: 2 below 2048 objects (more, smaller units for
+// the few objects there are), else 4.
+static SmallLaunch small_pick(int64_t n, bool f32, bool sum) {
+    if (n < 2048) {
+        if (f32) return sum ? small_launch_of<true, 2, true>() : small_launch_of<true, 2, false>();
+        return sum ? small_launch_of<false, 2, true>() : small_launch_of<false, 2, false>();
+    }
+    if (f32) return sum ? small_launch_of<true, 4, true>() : small_launch_of<true, 4, false>();
+    return sum ? small_launch_of<false, 4, true>() : small_launch_of<false, 4, false>();
+}
+
+struct SmallGeom {
+    int32_t K, units, grid;
+};
+
+static SmallGeom small_geometry(int64_t n, int R) {
+    SmallGeom g;
+    const int64_t T = 32 * R;
+    const int64_t h = (n - 1) / 2;
+    const int64_t M = (n + T - 1) / T;
+    g.K = static_cast<int32_t>((T + h + 1 + SMALL_JS - 1) / SMALL_JS);
+    g.units = static_cast<int32_t>(M * g.K);
+    g.grid = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>((g.units + SMALL_WARPS - 1) / SMALL_WARPS, static_cast<int64_t>(sm_count()) * 2)));
+    return g;
+}
+
+// ---------------------------------------------------------------------------------------
+// host side of the large-set path
+// ---------------------------------------------------------------------------------------
+
 struct Launch {
-    SingleCfg cfg;       // nt = objects' stride inside a tile; tile = cfg.nt * cfg.r
+    SingleCfg cfg;       // cfg.nt = 32 (objects' stride inside a warp tile); tile = 32 * cfg.r
     const void *fn;
     int smem;
     int blocks_per_sm;
     int threads;         // threads per CTA
-    int warp_units;      // 1: units are split per warp, 0: per CTA
 };
 
-template <int CLASS, int NT, int R, int JS, int NS, bool SUM, int MINB>
-static cc_status get_launch(Launch &L) {
-    static int bps = -1;
-    static int smem = SmemLayout<NT, R, JS, NS>::kTotal;
-    auto fn = k_pairs<CLASS, NT, R, JS, NS, SUM, MINB>;
-    if (bps < 0) {
-        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        int b = 0;
-        CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, NT + 32, smem));
-        bps = std::max(b, 1);
-    }
-    L.cfg = SingleCfg{NT, R, JS, NS};
-    L.fn = reinterpret_cast<const void *>(fn);
-    L.smem = smem;
-    L.blocks_per_sm = bps;
-    L.threads = NT + 32;
-    L.warp_units = 0;
-    return CC_OK;
-}
-
-template <int CLASS, int NW, int R, int JS, int NS, bool SUM, int MINB>
+template <int CLASS, int NW, int R, int JS, int NS, bool SUM>
 static cc_status get_launch_w(Launch &L) {
-    static int bps = -1;
-    static int smem = WarpSmem<NW, JS, NS>::kTotal;
-    auto fn = k_pairs_w<CLASS, NW, R, JS, NS, SUM, MINB>;
-    if (bps < 0) {
-        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    using S = WarpSmem<NW, JS, NS>;
+    // attribute and occupancy, once per instance (thread-safe static initialisation)
+    static const std::pair<cudaError_t, int> once = []() {
+        auto f = k_pairs_w<CLASS, NW, R, JS, NS, SUM, 1>;
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kTotal);
         int b = 0;
-        CC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, NW * 32, smem));
-        bps = std::max(b, 1);
-    }
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, NW * 32, S::kTotal);
+        return std::make_pair(e, std::max(b, 1));
+    }();
+    CC_CUDA(once.first);
     L.cfg = SingleCfg{32, R, JS, NS};
-    L.fn = reinterpret_cast<const void *>(fn);
-    L.smem = smem;
-    L.blocks_per_sm = bps;
+    L.fn = reinterpret_cast<const void *>(k_pairs_w<CLASS, NW, R, JS, NS, SUM, 1>);
+    L.smem = S::kTotal;
+    L.blocks_per_sm = once.second;
     L.threads = NW * 32;
-    L.warp_units = 1;
     return CC_OK;
 }
 
-// Tile shape of the large-set band; CC_SINGLE_VARIANT selects among the compiled shapes
-// (used by the tuning sweep; the default is the measured best).
-static int large_variant() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("CC_SINGLE_VARIANT");
-        v = e ? atoi(e) : -2;
-        if (v < -2 || v > 10) v = -2;
-    }
-    return v;
-}
-
-// Measured best large-set shape on GB300 for both classes: 12 warps x 8 objects per lane,
-// 256-object stages, 4-deep rings (with the object state kept in genuine register
-// pairs, see load_i).
-template <int CLASS>
-static int large_default() { return 4; }
-
+// FP32-pipe kernel shapes (warps per CTA, objects per lane, stage width, ring depth):
+// large sets 12 x 8 objects per lane, 256-object stages, 4-deep rings (the measured
+// best on GB300, with the object state kept in genuine register pairs, see load_i);
+// mid-size sets (from the small-set limit to 65536) 8 x 4, 128-object stages, 4-deep.
 template <int CLASS, bool SUM>
 static cc_status pick_class(int64_t n, Launch &L) {
-    if (n >= 65536) {
-        const int v = large_variant() >= 0 ? large_variant() : large_default<CLASS>();
-        switch (v) {
-            case 1: return get_launch<CLASS, 128, 8, 512, 6, SUM, 2>(L);
-            case 2: return get_launch<CLASS, 256, 4, 512, 6, SUM, 2>(L);
-            case 3: return get_launch<CLASS, 128, 4, 256, 8, SUM, 3>(L);
-            case 4: return get_launch_w<CLASS, 12, 8, 256, 4, SUM, 1>(L);
-            case 5: return get_launch_w<CLASS, 16, 4, 128, 4, SUM, 1>(L);
-            case 6: return get_launch_w<CLASS, 8, 8, 256, 4, SUM, 1>(L);
-            case 7: return get_launch_w<CLASS, 16, 4, 256, 3, SUM, 1>(L);
-            case 8: return get_launch_w<CLASS, 8, 8, 256, 4, SUM, 2>(L);
-            case 9: return get_launch_w<CLASS, 12, 6, 256, 4, SUM, 1>(L);
-            case 10: return get_launch_w<CLASS, 8, 8, 512, 3, SUM, 1>(L);
-            default: return get_launch<CLASS, 256, 8, 512, 6, SUM, 1>(L);
-        }
-    }
-    if (n >= 2048) return get_launch<CLASS, 128, 4, 128, 6, SUM, 2>(L);
-    return get_launch<CLASS, 64, 2, 64, 4, SUM, 2>(L);
+    if (n >= 65536) return get_launch_w<CLASS, 12, 8, 256, 4, SUM>(L);
+    return get_launch_w<CLASS, 8, 4, 128, 4, SUM>(L);
 }
 
 // Geometry of one call.
@@ -884,7 +1009,7 @@ static Geometry geometry(int64_t n, const Launch &L) {
     const int64_t elen = (g.M - 1) * T + g.K * L.cfg.js;
     g.nrec = elen / 2;
     const int64_t slots = static_cast<int64_t>(sm_count()) * L.blocks_per_sm;
-    const int64_t per_cta = L.warp_units ? L.threads / 32 : 1;
+    const int64_t per_cta = L.threads / 32;   // units are split per warp
     g.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((g.units + per_cta - 1) / per_cta, slots)));
     return g;
 }
@@ -894,25 +1019,79 @@ static cc_status pick_launch(int64_t n, bool f32, bool sum, Launch &L) {
     return sum ? pick_class<CLASS_I32, true>(n, L) : pick_class<CLASS_I32, false>(n, L);
 }
 
-static bool use_tc(int64_t n, bool sum, bool allow_tc) {
-    (void)sum;   // counts and interaction sums alike
-    return allow_tc && n >= tc_min_n() && tc_enabled();
+static bool use_tc(int64_t n, bool allow_tc) { return allow_tc && n >= tc_min_n() && tc_enabled(); }
+
+// Sets below this size take the one-launch small-set kernel.
+static bool use_small(int64_t n) { return n < tc_min_n(); }
+
+// Record region and per-CTA slots of the large-set path: the larger over both kernel
+// classes (and the tensor-core operands when they may run), so that one workspace serves
+// counts and sums of either dtype.
+struct Regions {
+    size_t region, slots;
+};
+
+static cc_status large_regions(int64_t n, bool sum, bool tc, Regions &R) {
+    R.region = 0;
+    R.slots = static_cast<size_t>(sm_count());
+    for (bool f32 : {false, true}) {
+        Launch L;
+        const cc_status st = pick_launch(n, f32, sum, L);
+        if (st != CC_OK) return st;
+        const Geometry g = geometry(n, L);
+        R.region = std::max(R.region, static_cast<size_t>(g.nrec) * sizeof(Rec));
+        R.slots = std::max(R.slots, static_cast<size_t>(g.grid));
+    }
+    if (tc) R.region = std::max(R.region, tc_region_bytes(n));
+    R.region = (R.region + 255) & ~static_cast<size_t>(255);
+    return CC_OK;
 }
 
 // Workspace layout: WsHeader | region | double partial[slots] | uint32 hist[TC_HIST_CELLS],
 // where the region holds the extended record array or (tensor-core mode) the two operand
-// arrays, and the histogram is the integer tensor-core path's occupancy count.
+// arrays, and the histogram is the integer tensor-core path's occupancy count. Small
+// sets: WsHeader | u64 count slots | FP64 sum slots (one each per CTA).
 size_t single_ws_bytes(int64_t n, bool sum, bool allow_tc) {
     if (n < 2) return sizeof(WsHeader);
-    // the geometry depends only on the tile shape, which is the same for both classes
-    Launch L;
-    if (pick_launch(n, false, sum, L) != CC_OK) return 0;
-    Geometry g = geometry(n, L);
-    size_t region = static_cast<size_t>(g.nrec) * sizeof(Rec);
-    if (use_tc(n, sum, allow_tc)) region = std::max(region, tc_region_bytes(n));
-    region = (region + 255) & ~static_cast<size_t>(255);
-    const size_t slots = static_cast<size_t>(std::max<int64_t>(g.grid, sm_count()));   // CTAs of either kernel
-    return sizeof(WsHeader) + region + slots * sizeof(double) + TC_HIST_CELLS * sizeof(uint32_t) + 256;
+    if (use_small(n)) {
+        const size_t slots = static_cast<size_t>(sm_count()) * 2;
+        return sizeof(WsHeader) + slots * (sizeof(unsigned long long) + sizeof(double)) + 256;
+    }
+    Regions R;
+    if (large_regions(n, sum, use_tc(n, allow_tc), R) != CC_OK) return 0;
+    return sizeof(WsHeader) + R.region + R.slots * sizeof(double) + TC_HIST_CELLS * sizeof(uint32_t) + 256;
+}
+
+static cc_status small_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned long long *d_count,
+                               float *d_sum, void *ws, cudaStream_t stream) {
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const bool f32 = p->dtype == CC_F32;
+    const SmallLaunch L = small_pick(n, f32, d_sum != nullptr);
+    const SmallGeom g = small_geometry(n, L.R);
+    const size_t slots = static_cast<size_t>(sm_count()) * 2;
+    uint8_t *base = reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader);
+    SmallArgs A;
+    A.x = p->x;
+    A.y = p->y;
+    A.z = p->z;
+    A.r = f32 ? p->r : nullptr;
+    A.n = static_cast<int32_t>(n);
+    A.h = static_cast<int32_t>((n - 1) / 2);
+    A.K = g.K;
+    A.units = g.units;
+    A.r2 = r2;
+    A.hdr = hdr;
+    A.slot_cnt = reinterpret_cast<unsigned long long *>(base);
+    A.slot_sum = reinterpret_cast<double *>(base + slots * sizeof(unsigned long long));
+    A.d_count = d_count;
+    A.d_sum = d_sum;
+    void *args[] = {&A};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool prof = profiling();
+    if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
+    CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(SMALL_WARPS * 32), args, 0, stream));
+    if (prof) profile_end(stream, e0, e1);
+    return CC_OK;
 }
 
 // Enqueues the whole single-set path on `stream` using workspace `ws` (>= single_ws_bytes).
@@ -920,6 +1099,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
                          float *d_sum, void *ws, cudaStream_t stream, bool allow_tc) {
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const bool f32 = p->dtype == CC_F32;
+    if (n >= 2 && use_small(n)) return small_enqueue(p, n, r2, d_count, d_sum, ws, stream);
     k_reset<<<1, 32, 0, stream>>>(hdr, f32 ? MODE_F32 : MODE_I32_FAST, d_count, d_sum);
     CC_CUDA(cudaGetLastError());
     if (n < 2) return CC_OK;
@@ -928,15 +1108,14 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     cc_status st = pick_launch(n, f32, sum, L);
     if (st != CC_OK) return st;
     Geometry g = geometry(n, L);
-    const bool tc = use_tc(n, sum, allow_tc);
+    const bool tc = use_tc(n, allow_tc);
+    Regions R;
+    st = large_regions(n, sum, tc, R);
+    if (st != CC_OK) return st;
     uint8_t *region = reinterpret_cast<uint8_t *>(ws) + sizeof(WsHeader);
-    size_t region_bytes = static_cast<size_t>(g.nrec) * sizeof(Rec);
-    if (tc) region_bytes = std::max(region_bytes, tc_region_bytes(n));
-    region_bytes = (region_bytes + 255) & ~static_cast<size_t>(255);
     Rec *E = reinterpret_cast<Rec *>(region);
-    double *partial = reinterpret_cast<double *>(region + region_bytes);
-    const size_t slots = static_cast<size_t>(std::max<int64_t>(g.grid, sm_count()));   // as in single_ws_bytes
-    uint32_t *hist = reinterpret_cast<uint32_t *>(partial + slots);
+    double *partial = reinterpret_cast<double *>(region + R.region);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(partial + R.slots);
     const int prep_threads = 256;
     const int64_t prep_blocks_full = (g.nrec + prep_threads - 1) / prep_threads;
     const int prep_blocks = static_cast<int>(std::min<int64_t>(prep_blocks_full, sm_count() * 8));
@@ -999,6 +1178,8 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     }
     CC_CUDA(cudaLaunchKernel(L.fn, dim3(g.grid), dim3(L.threads), args, L.smem, stream));
     if (prof) profile_end(stream, e0, e1);
+    k_finalize<<<1, 32, 0, stream>>>(hdr, d_count, d_sum);
+    CC_CUDA(cudaGetLastError());
     return CC_OK;
 }
 
@@ -1039,11 +1220,12 @@ cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned 
     using L = WarpSmem<NW, JS, NS>;
     const void *fn = f32 ? reinterpret_cast<const void *>(k_pairs_straight<CLASS_F32, NW, R, JS, NS>)
                          : reinterpret_cast<const void *>(k_pairs_straight<CLASS_I32, NW, R, JS, NS>);
-    static bool attr_done[2] = {false, false};
-    if (!attr_done[f32 ? 1 : 0]) {
-        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal));
-        attr_done[f32 ? 1 : 0] = true;
-    }
+    // shared-memory attribute, once per kernel class (thread-safe static initialisation)
+    static const cudaError_t attr_i32 = cudaFuncSetAttribute(
+        k_pairs_straight<CLASS_I32, NW, R, JS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+    static const cudaError_t attr_f32 = cudaFuncSetAttribute(
+        k_pairs_straight<CLASS_F32, NW, R, JS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+    CC_CUDA(f32 ? attr_f32 : attr_i32);
     PairArgs A{};
     A.E = E;
     A.n = n;
@@ -1060,6 +1242,8 @@ cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned 
     if (prof) CC_CUDA(profile_begin(stream, &e0, &e1));
     CC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(NW * 32), args, L::kTotal, stream));
     if (prof) profile_end(stream, e0, e1);
+    k_finalize<<<1, 32, 0, stream>>>(hdr, d_count, nullptr);
+    CC_CUDA(cudaGetLastError());
     return CC_OK;
 }
 

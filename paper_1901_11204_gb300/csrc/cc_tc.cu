@@ -476,12 +476,12 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 if (!STEW && (new_tile || q + 1 == nu)) tc_commit(&a_empty[as]);
             }
             if (!ok) {
-                atomicOr(&A.hdr->status, ST_TIMEOUT);
+                flag_status(A.hdr, ST_TIMEOUT);
                 *abort_flag = 1;
             }
             // all MMAs issued by this thread complete before TMEM is freed
             tc_commit(done);
-            if (!mbar_wait_bounded(done, 0u, A.wait_ns)) atomicOr(&A.hdr->status, ST_TIMEOUT);
+            if (!mbar_wait_bounded(done, 0u, A.wait_ns)) flag_status(A.hdr, ST_TIMEOUT);
         }
     } else {
         // ------------------------------- epilogue warps --------------------------------
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                                                           : mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
-                    atomicOr(&A.hdr->status, ST_TIMEOUT);
+                    flag_status(A.hdr, ST_TIMEOUT);
                     *abort_flag = 1;
                 }
                 break;
@@ -760,52 +760,38 @@ template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool S
 static cc_status tc_launch_of(TcLaunch &L) {
     static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
     auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC, TRYW, CF>;
-    static bool attr = false;
-    if (!attr) {
-        CC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ));
-        attr = true;
-    }
+    // shared-memory attribute, once per instance (thread-safe static initialisation)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ);
+    CC_CUDA(attr);
     L.fn = reinterpret_cast<const void *>(fn);
     L.js = JS;
     L.threads = (2 + EPW) * 32;
     return CC_OK;
 }
 
-// Compiled shapes (CC_TC_VARIANT selects one for sweeps; the default is the measured best).
-static int tc_variant() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("CC_TC_VARIANT");
-        v = e ? atoi(e) : 0;
-        if (v < 0 || v > 9) v = 0;
-    }
-    return v;
-}
+// The compiled shapes, all 256-object stages (MMA N), two 256-column accumulators, eight
+// epilogue warps, a 12-deep j-stage ring, early barrier tests, epilogue slot returns,
+// min-reducing TMEM loads, sleeping waits in the epilogue and copy warps and the
+// accumulator's commit before the early tests (template arguments: JS, NB, EPW, NS, SCR,
+// PRE, STEW, SUMT, SPH, RED, WALKC, TRYW, CF). They differ in the epilogue: the integer
+// count in registers (dense hits) or by the walk (sparse hits), the integer interaction
+// sum, and the FP32 sphere count and sum (walks behind the integer screen). The
+// alternatives measured slower on GB300 are listed with their rates in the design notes.
+enum class TcForm { CountRegisters, CountWalk, Sum, SphereCount, SphereSum };
 
-static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
-    // Template arguments: stage width JS, accumulators NB, epilogue warps EPW, ring depth NS,
-    // values screened on the ALU SCR, early barrier tests PRE, epilogue slot returns STEW,
-    // interaction sum SUMT, sphere screen SPH, min-reducing TMEM loads RED, count by walk
-    // WALKC, sleeping waits in the epilogue and copy warps TRYW, the accumulator's commit
-    // before the early barrier tests CF. Sums and spheres walk the screened values;
-    // counts take CC_TC_VARIANT (0: the in-register form here, launched beside the walk
-    // form by tc_enqueue_pairs, the device choosing between them).
-    if (sph) {
-        return sum ? tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true, true>(L)
-                   : tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true, true>(L);
-    }
-    if (sum) return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true, false, true, true>(L);
-    switch (tc_variant()) {
-        case 1: return tc_launch_of<256, 2, 8, 12>(L);   // MMA thread tests and commits everything
-        case 2: return tc_launch_of<128, 4, 8, 16, 0, true, true>(L);
-        case 3: return tc_launch_of<256, 2, 16, 12, 0, true, true>(L);
-        case 4: return tc_launch_of<256, 2, 8, 12, 64, true, true>(L);
-        case 5: return tc_launch_of<256, 2, 8, 12, 0, true, true>(L);   // every value counted by FMA
-        case 6: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true>(L);
-        case 7: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true>(L);   // spinning waits
-        case 8: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true>(L);   // commit after the tests
-        case 9: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true, true, true>(L);   // walk form only
-        default: return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true, true>(L);
+static cc_status tc_form_launch(TcLaunch &L, TcForm f) {
+    switch (f) {
+        case TcForm::CountRegisters:
+            return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true, true>(L);
+        case TcForm::CountWalk:
+            return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true, true, true>(L);
+        case TcForm::Sum:
+            return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true, false, true, true>(L);
+        case TcForm::SphereCount:
+            return tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true, true>(L);
+        default:
+            return tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true, true>(L);
     }
 }
 
@@ -815,7 +801,7 @@ static cc_status tc_pick(TcLaunch &L, bool sum, bool sph) {
 cc_status tc_enqueue_fill(const cc_points *p, int64_t n, uint8_t *region, WsHeader *hdr, uint32_t *hist,
                           cudaStream_t stream) {
     TcLaunch L;
-    cc_status st = tc_pick(L, false, false);   // every form has the same stage width
+    cc_status st = tc_form_launch(L, TcForm::CountWalk);   // every form has the same stage width
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
     const int64_t rows = std::max<int64_t>(g.M * TC_T, g.elen);
@@ -837,7 +823,9 @@ cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region,
                            unsigned long long *d_count, float *d_sum, double *partial, cudaStream_t stream) {
     TcLaunch L;
     const bool sph = p->dtype == CC_F32;
-    cc_status st = tc_pick(L, d_sum != nullptr, sph);
+    const bool sum = d_sum != nullptr;
+    cc_status st = tc_form_launch(L, sph ? (sum ? TcForm::SphereSum : TcForm::SphereCount)
+                                         : (sum ? TcForm::Sum : TcForm::CountRegisters));
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
     TcArgs A;
@@ -860,11 +848,11 @@ cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region,
     A.form = -1;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g.units, sm_count())));
     void *args[] = {&A};
-    if (!sph && d_sum == nullptr && tc_variant() == 0) {
-        // integer count, default shape: both count forms are launched and the one the
-        // preparation kernel chose (hdr->tc_form, from the expected hit density) runs
+    if (!sph && !sum) {
+        // integer count: both count forms are launched and the one the preparation
+        // kernel chose (hdr->tc_form, from the expected hit density) runs
         TcLaunch W;
-        st = tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true, true, true>(W);
+        st = tc_form_launch(W, TcForm::CountWalk);
         if (st != CC_OK) return st;
         A.form = 0;
         CC_CUDA(cudaLaunchKernel(L.fn, dim3(grid), dim3(L.threads), args, TC_SMEM_REQ, stream));

@@ -164,3 +164,36 @@ def test_large_sets_in_the_mix(cc):
             for r in (res[rid], res2[rid + 10000]):
                 assert abs(r["sum"] - want_s) <= 1e-5 * want_s, (k, r["sum"], want_s)
     srv.close()
+
+
+def test_single_route_timeout_is_reported(cc):
+    """A bounded wait that runs out on the single-set route (a set of n >= 16384 on the
+    tensor cores, copies held back by the test hook): that request's result carries
+    CC_ERR_TIMEOUT, count CC_COUNT_INVALID and a NaN sum; a small set served in the same
+    batch is exact; after the hook is released the same queries are exact again."""
+    rng = np.random.default_rng(31)
+    n = 20000
+    big = tuple(rng.integers(0, 1024, n).astype(np.int32) for _ in range(3))
+    small = tuple(rng.integers(0, 20, 500).astype(np.int32) for _ in range(3))
+    srv = cc.Server(1 << 30, 64)
+    sb = srv.register_set(*big)
+    ss = srv.register_set(*small)
+    cc.set_wait_limit_ns(20_000_000)
+    cc.debug_stall_copies(True)
+    try:
+        res = run_requests(srv, [(sb, cc.CC_OP_COUNT, 9, 0), (sb, cc.CC_OP_SUM, 9, 1),
+                                 (ss, cc.CC_OP_COUNT, 9, 2)])
+    finally:
+        cc.debug_stall_copies(False)
+        cc.set_wait_limit_ns(2_000_000_000)
+    for k in (0, 1):
+        assert res[k]["status"] == cc.CC_ERR_TIMEOUT, res[k]
+        assert res[k]["count"] == cc.CC_COUNT_INVALID
+    assert np.isnan(res[1]["sum"])
+    assert res[2]["status"] == cc.CC_OK and res[2]["count"] == oracle.count_i32(*small, 9)
+    res = run_requests(srv, [(sb, cc.CC_OP_COUNT, 9, 3), (sb, cc.CC_OP_SUM, 9, 4)])
+    want_c, want_s = oracle.sum_i32(*big, 9)
+    assert res[3]["status"] == cc.CC_OK and res[3]["count"] == want_c
+    assert res[4]["status"] == cc.CC_OK and res[4]["count"] == want_c
+    assert abs(res[4]["sum"] - want_s) <= 1e-5 * want_s
+    srv.close()

@@ -181,21 +181,61 @@ def test_stream_and_repeat_determinism(cc):
     assert len(vals) == 1
 
 
-def test_bounded_wait_timeout(cc):
-    """The copy issuer holds back every copy: consumers' waits run out after the short
-    limit, the kernel returns, the status reads CC_ERR_TIMEOUT and the context still works."""
-    c = synth.cfg1()
-    t = dev(c["x"], c["y"], c["z"])
+@pytest.mark.parametrize("kind", ["i32", "f32"])
+def test_bounded_wait_timeout(cc, kind):
+    """The FP32-pipe kernel's copy issuers hold back every copy: the warps' waits run out
+    after the short limit, the kernel returns, the count reads CC_COUNT_INVALID (the sum
+    NaN), the status CC_ERR_TIMEOUT, and the context still works."""
+    n = 20001
+    if kind == "i32":
+        c = synth.cfg2(n)
+        arrs, r2 = [c["x"], c["y"], c["z"]], 9
+        want = oracle.count_i32(*arrs, r2)
+    else:
+        arrs = list(synth.sphere_points(n, 41, rmin=0.002, rmax=0.006))
+        r2 = 0
+        want = oracle.count_f32(*arrs)[0]
+    t = dev(*arrs)
+    r = t[3] if kind == "f32" else None
+    cc.set_tensor_cores(False)
     cc.set_wait_limit_ns(20_000_000)
     cc.debug_stall_copies(True)
     try:
-        cc.count_pairs(*t, r2=16)
+        out = cc.count_pairs(*t[:3], r2=r2, r=r)
         assert cc.stream_status() == cc.CC_ERR_TIMEOUT
+        assert cc.as_u64(out) == cc.CC_COUNT_INVALID
+        s, c2 = cc.interaction_sum(*t[:3], r2=r2, r=r)
+        assert cc.stream_status() == cc.CC_ERR_TIMEOUT
+        assert cc.as_u64(c2) == cc.CC_COUNT_INVALID
+        assert np.isnan(float(s.item()))
     finally:
         cc.debug_stall_copies(False)
         cc.set_wait_limit_ns(2_000_000_000)
+        cc.set_tensor_cores(True)
+    # the next calls on the same stream are correct and report no error
+    out = cc.count_pairs(*t[:3], r2=r2, r=r)
+    torch.cuda.synchronize()
+    assert cc.as_u64(out) == want
+    assert cc.stream_status() == cc.CC_OK
+
+
+def test_small_set_kernel_reports_range_and_recovers(cc):
+    """The one-launch kernel for small sets: a span beyond 32767 gives CC_COUNT_INVALID
+    and CC_ERR_RANGE; its header words are left clean, so the next small and large calls
+    on the stream are exact."""
+    c = synth.cfg1()
+    t = dev(c["x"], c["y"], c["z"])
+    bad = c["x"].copy()
+    bad[17] = 40000
+    tb = dev(bad, c["y"], c["z"])
+    out = cc.count_pairs(*tb, r2=16)
+    assert cc.stream_status() == cc.CC_ERR_RANGE
+    assert cc.as_u64(out) == cc.CC_COUNT_INVALID
+    assert cc.stream_mode() == cc.MODE_RANGE_ERROR
     assert gpu_count(cc, c["x"], c["y"], c["z"], 16) == oracle.count_i32(c["x"], c["y"], c["z"], 16)
     assert cc.stream_status() == cc.CC_OK
+    c2 = synth.cfg2(20001)
+    assert gpu_count(cc, c2["x"], c2["y"], c2["z"], 9) == oracle.count_i32(c2["x"], c2["y"], c2["z"], 9)
 
 
 def _golden():

@@ -232,16 +232,22 @@ def test_clustered_sets(cc, frac):
 
 def test_tc_bounded_wait_timeout(cc):
     """No copy is issued: the MMA lane's wait runs out, every role stops, TMEM is freed,
-    the status reads CC_ERR_TIMEOUT and the next call is correct."""
+    the count reads CC_COUNT_INVALID (the sum NaN), the status CC_ERR_TIMEOUT, and the
+    next call is correct."""
     rng = np.random.default_rng(11)
     x, y, z = box_points(rng, 20000, 1023)
     t = dev(x, y, z)
     cc.set_wait_limit_ns(20_000_000)
     cc.debug_stall_copies(True)
     try:
-        cc.count_pairs(*t, r2=9)
+        out = cc.count_pairs(*t, r2=9)
         assert cc.stream_status() == cc.CC_ERR_TIMEOUT
         assert cc.stream_mode() == cc.MODE_TENSOR
+        assert cc.as_u64(out) == cc.CC_COUNT_INVALID
+        s, c = cc.interaction_sum(*t, r2=9)
+        assert cc.stream_status() == cc.CC_ERR_TIMEOUT
+        assert cc.as_u64(c) == cc.CC_COUNT_INVALID
+        assert np.isnan(float(s.item()))
     finally:
         cc.debug_stall_copies(False)
         cc.set_wait_limit_ns(2_000_000_000)
