@@ -111,9 +111,26 @@ __host__ __device__ __forceinline__ int64_t stages_of(const Band &b, int64_t n) 
     return (tile_of(b) + h + 1 + kJSB - 1) / kJSB;
 }
 
+// Most work items one set may produce, beyond one per tile: without a bound the items of a
+// set would grow with n^2 (tiles times chunks), and with them the queue a plan reserves.
+constexpr int64_t kMaxItemsPerSet = 16384;
+
+// Stages (of kJSB objects) per work item: the band's sc (0 = the whole tile range),
+// widened where needed so that a set has at most max(tiles, kMaxItemsPerSet) items.
+__host__ __device__ __forceinline__ int64_t chunk_stages(const Band &b, int64_t n) {
+    const int64_t K = stages_of(b, n);
+    const int64_t T = tile_of(b);
+    const int64_t M = (n + T - 1) / T;
+    int64_t per = b.sc > 0 ? b.sc : K;
+    const int64_t maxch = kMaxItemsPerSet / M > 1 ? kMaxItemsPerSet / M : 1;
+    if ((K + per - 1) / per > maxch) per = (K + maxch - 1) / maxch;
+    return per;
+}
+
 __host__ __device__ __forceinline__ int64_t chunks_of(const Band &b, int64_t n) {
     const int64_t K = stages_of(b, n);
-    return b.sc > 0 ? (K + b.sc - 1) / b.sc : 1;
+    const int64_t per = chunk_stages(b, n);
+    return (K + per - 1) / per;
 }
 
 __host__ __device__ __forceinline__ int64_t items_of(const Band &b, int64_t n) {
@@ -322,8 +339,9 @@ __device__ void run_item(const SetDesc &d, const SetAux &x, const Band &b, int32
     const int32_t K = static_cast<int32_t>(stages_of(b, n));
     const int32_t tile = local % M;
     const int32_t chunk = local / M;
-    const int32_t k0 = b.sc > 0 ? chunk * b.sc : 0;
-    const int32_t k1 = b.sc > 0 ? min(k0 + b.sc, K) : K;
+    const int32_t per = static_cast<int32_t>(chunk_stages(b, n));
+    const int32_t k0 = chunk * per;
+    const int32_t k1 = min(k0 + per, K);
     const int32_t tile0 = tile * T;
     const RawSet rs{d.x, d.y, d.z, d.r, n, x.cx, x.cy, x.cz, x.ai_off};
     IState<R> s;

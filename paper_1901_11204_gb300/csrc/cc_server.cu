@@ -90,7 +90,9 @@ struct Lane {
 };
 
 constexpr int kLanes = 2;
-constexpr int64_t kPlanMaxPoints = int64_t(1) << 26;
+// Points per batch (sizes each lane's work queue: about 200 MB per lane at 2^24); sets
+// larger than this always take the single-set route.
+constexpr int64_t kPlanMaxPoints = int64_t(1) << 24;
 
 }  // namespace
 
@@ -354,15 +356,19 @@ cc_status cc_server_register_set(cc_server *S, const cc_points *p, int64_t n, in
         if (S->resident_bytes + S->inflight_bytes + bytes > S->budget)
             return fail(CC_ERR_NOMEM, "memory budget exceeded by this set");
         S->resident_bytes += bytes;
-        if (n >= kServerTcMinN && tc_enabled()) {
+        if (n >= kServerTcMinN && (tc_enabled() || n > kPlanMaxPoints)) {
             // both lanes may hold a workspace of this size (allocated by the scheduler on
-            // first use); without room in the budget the set stays on the batched path
+            // first use); without room in the budget the set stays on the batched path,
+            // unless it is too large for a batch
             const size_t need = 2 * std::max(single_ws_bytes(n, false, true), single_ws_bytes(n, true, true));
             const size_t extra = need > S->single_ws_reserved ? need - S->single_ws_reserved : 0;
             if (S->resident_bytes + S->inflight_bytes + extra <= S->budget) {
                 S->resident_bytes += extra;
                 S->single_ws_reserved += extra;
                 single = true;
+            } else if (n > kPlanMaxPoints) {
+                S->resident_bytes -= bytes;
+                return fail(CC_ERR_NOMEM, "memory budget too small for the workspace of a set this large");
             }
         }
     }

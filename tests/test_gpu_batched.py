@@ -138,3 +138,15 @@ def test_cfg4_full(cc):
     assert np.array_equal(counts.cpu().numpy().view(np.uint64), want)
     assert plan.last_items() > 0
     plan.close()
+
+
+def test_plan_memory_is_bounded(cc):
+    """A plan for 4096 sets of up to 2^24 points in all reserves its work queue for at most
+    max(tiles, 16384) items per set: a few hundred MB, not a queue that grows with n^2."""
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    plan = cc.Plan(4096, 1 << 24, cc.default_tune_table())
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    plan.close()
+    assert used < (512 << 20), used
