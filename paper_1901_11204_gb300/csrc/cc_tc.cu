@@ -222,18 +222,31 @@ struct TcArgs {
                             // this (0 or 1); -1 runs whatever the form
 };
 
-template <int JS, int NB, int EPW, int NS>
+// Shape of the kernel: j-stages of TC_JS objects (the MMA's N), TC_NB accumulators of
+// TC_JS TMEM columns (TC_NB * TC_JS = 512, all of TMEM), TC_EPW epilogue warps (two per
+// TMEM lane quarter, TC_CPW columns each), a TC_NS-deep ring of j-stages.
+constexpr int TC_JS = 256;
+constexpr int TC_NB = 2;
+constexpr int TC_EPW = 8;
+constexpr int TC_NS = 12;
+constexpr int TC_CPW = TC_JS / (TC_EPW / 4);   // accumulator columns per epilogue warp and unit
+// warps: copy, MMA, TC_EPW epilogue warps (warps 2 .. 2 + TC_EPW - 1, so that warp & 3 is the
+// TMEM lane quarter each may read), and one slot-return warp
+constexpr int TC_THREADS = (3 + TC_EPW) * 32;
+static_assert(TC_NB * TC_JS == 512, "the accumulators fill the 512 TMEM columns");
+static_assert(TC_NS > TC_NB, "a unit's stage slot outlives the release of its accumulator");
+
 struct TcSmem {
-    static constexpr int kStage = JS * TC_ROW;            // bytes of one j-stage
+    static constexpr int kStage = TC_JS * TC_ROW;         // bytes of one j-stage
     static constexpr int kA = 0;                          // 2 i-tile slots
-    static constexpr int kB = 2 * TC_ATILE;               // NS j-stage slots
-    static constexpr int kBars = kB + NS * kStage;
-    // a_full[2] a_empty[2] b_full[NS] b_empty[NS] t_full[NB] t_empty[NB] done
-    static constexpr int kNBars = 5 + 2 * NS + 2 * NB;
-    static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag
+    static constexpr int kB = 2 * TC_ATILE;               // TC_NS j-stage slots
+    static constexpr int kBars = kB + TC_NS * kStage;
+    // a_full[2] a_empty[2] ready[NS] b_empty[NS] t_full[NB] done
+    static constexpr int kNBars = 5 + 2 * TC_NS + TC_NB;
+    static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag, copy drain words
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
-    static constexpr int kRedSum = kRed + EPW * 8;        // per-epilogue-warp sums
-    static constexpr int kTotal = kRedSum + EPW * 8;
+    static constexpr int kRedSum = kRed + TC_EPW * 8;     // per-epilogue-warp sums
+    static constexpr int kTotal = kRedSum + TC_EPW * 8;
 };
 
 __device__ __forceinline__ f2 f2_fma_rm(f2 a, f2 b, f2 c) {
@@ -281,58 +294,61 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = t;
 }
 
-// JS objects per j-stage (MMA N), NB accumulators of JS TMEM columns (NB * JS = 512),
-// EPW epilogue warps, NS-deep j-stage ring. Of each epilogue thread's CPW values per
-// unit, SCR are screened on the integer ALU (a three-input OR of the raw bits per two
-// values; a set sign bit sends that group to an exact recount, rare unless hits are
-// dense) and the rest counted exactly on the FP32 pipe, so the two pipes share the work.
-// PRE: the MMA thread tests the next unit's barriers right after issuing the current
-// MMA (CF: after committing the accumulator's barrier, so that the epilogue hears of the
-// MMA sooner; otherwise before the commits). STEW: the first epilogue thread, not the
-// MMA thread, returns each j-stage slot and each i-tile slot (plain arrivals once it has
-// seen the completion of the MMAs that read them), leaving the MMA thread one commit per
-// unit. The MMA
-// thread is the pipeline's critical path (it shares its SMSP with two counting warps);
-// both measured faster and are on in the default shape.
-// RED (default): the accumulator is read with tcgen05.ld.red .min, which also gives each
-// thread the minimum of its 128 values; a warp whose minimum is non-negative everywhere
-// (every pair of the block misses) skips the count, so the FMA-pipe counting runs only
-// for warps that hold a hit (+30 % at low hit density, +4 % at one hit per 30,000 pairs).
-// WALKC: such warps count by the walk below instead; no value then stays live past the
-// load, a leaner loop that is 9 % faster at 1e-7 hits per pair and 19 % slower at 3e-5.
-// The host launches both count forms and each runs only when the preparation kernel
-// chose it (hdr->tc_form, from the expected hit density; TcArgs::form).
-// SUMT: the interaction sum as well; SPH: FP32 spheres, the integer form being a screen.
-// Where the warp holds a negative value, the groups of 8 columns that hold one are
-// re-read from TMEM and walked exactly before the accumulator is handed back: for sums,
-// counting and adding 1/max(d, 1e-6) with d^2 = v + r2e + 1 exact in FP32, in a
-// Kahan-compensated FP32 sum per thread; for spheres, applying the FP32 predicate to the
-// pair's own coordinates. (Walking the register copy instead, with the accumulator
-// handed back at once, keeps all 128 values live through the walk: it spilled and
-// measured slower at every hit density.)
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
-          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false, bool CF = false>
-__global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
-    using L = TcSmem<JS, NB, EPW, NS>;
-    static_assert(NB * JS == 512, "the accumulators fill the 512 TMEM columns");
-    static_assert(EPW % 4 == 0, "epilogue warps cover the four TMEM lane quarters equally");
-    constexpr int CPW = JS / (EPW / 4);   // accumulator columns per epilogue warp and unit
-    static_assert(CPW == 32 || CPW == 64 || CPW == 128, "one TMEM load per epilogue warp and unit");
+// The epilogue forms. Every form reads the accumulator with tcgen05.ld.red .min, which
+// also gives each thread the minimum of its 128 values: a warp whose minima are all
+// non-negative (every pair of its block misses, the common case at collision radii)
+// only votes.
+//   WALK = false (integer count, dense hits): the buffer is handed back right after the
+//     load and warps holding a negative value count their 128 values with the rounding-
+//     down packed FMA on the accumulators in registers.
+//   WALK = true (integer count at sparse hits; interaction sums SUMT; FP32 spheres SPH):
+//     warps holding a negative value OR each group of 8 columns, re-read the flagged
+//     groups from TMEM (the accumulator is still held) and walk them exactly: count the
+//     negatives inside the row's schedule window; for sums add 1/max(d, 1e-6) with
+//     d^2 = v + r2e + 1 (exact in FP32) to a Kahan-compensated FP32 sum per thread; for
+//     spheres apply the FP32 predicate to the pair's own coordinates. No value stays
+//     live past the load, so the loop stays lean.
+// The host launches both integer count forms and each runs only when the preparation
+// kernel chose it (hdr->tc_form, from the expected hit density; TcArgs::form).
+//
+// Barriers (mbarrier, shared memory):
+//   a_full/a_empty[2]  i-tile slots: copied by warp 0, freed by the slot-return warp
+//                      once the tile's last MMA of this CTA completed;
+//   ready[NS]          unit q may run: the stage copy of q landed (the copy warp's
+//                      arrive.expect_tx and the copy's bytes) AND every epilogue warp
+//                      released the accumulator unit q will overwrite (the one of unit
+//                      q - NB; arrive count 1 + EPW, the first NB units pre-arrived), so
+//                      that the MMA thread, the pipeline's critical path, tests one
+//                      barrier per unit;
+//   b_empty[NS]        stage slot free again: the slot-return warp, once unit q's MMA
+//                      completed (a warp of its own, so that the epilogue warps, which all
+//                      must release an accumulator before the next MMA into it, do equal
+//                      work: an epilogue warp with this extra duty was measured to trail
+//                      the others by about 300 cycles per unit and pace the pipeline);
+//   t_full[NB]         accumulator written: tcgen05.commit after the unit's MMA;
+//   done               every MMA of this CTA completed (before TMEM is freed).
+template <bool SUMT, bool SPH, bool WALKC>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
+    using L = TcSmem;
+    constexpr int JS = TC_JS, NB = TC_NB, EPW = TC_EPW, NS = TC_NS, CPW = TC_CPW;
     constexpr int kStage = L::kStage;
+    constexpr bool WALK = SUMT || SPH || WALKC;   // screened values are walked one by one
     extern __shared__ __align__(1024) uint8_t smem[];
     // uniform: another kernel handles this call
     if (A.hdr->mode != (SPH ? MODE_F32_TC : MODE_I32_TC)) return;
     if (A.form >= 0 && A.hdr->tc_form != A.form) return;   // the other count form runs
-    constexpr bool WALK = SUMT || SPH || WALKC;   // screened values are walked one by one
 
     uint8_t *sA = smem + L::kA;
     uint8_t *sB = smem + L::kB;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
     uint64_t *a_full = bars, *a_empty = bars + 2;
-    uint64_t *b_full = bars + 4, *b_empty = bars + 4 + NS;
-    uint64_t *t_full = bars + 4 + 2 * NS, *t_empty = t_full + NB, *done = t_full + 2 * NB;
+    uint64_t *ready = bars + 4, *b_empty = bars + 4 + NS;
+    uint64_t *t_full = bars + 4 + 2 * NS, *done = t_full + NB;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
+    // the copy warp's number of issued stage copies, published when it stops (drain)
+    volatile int *copy_issued = reinterpret_cast<volatile int *>(smem + L::kMisc + 8);
+    volatile int *copy_stopped = reinterpret_cast<volatile int *>(smem + L::kMisc + 12);
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem + L::kRed);
     double *red_sum = reinterpret_cast<double *>(smem + L::kRedSum);
 
@@ -342,16 +358,15 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
-        for (int i = 0; i < NB; ++i) {
-            mbar_init(&t_full[i], 1);
-            mbar_init(&t_empty[i], EPW);
-        }
+        for (int i = 0; i < NB; ++i) mbar_init(&t_full[i], 1);
         for (int i = 0; i < NS; ++i) {
-            mbar_init(&b_full[i], 1);
+            mbar_init(&ready[i], 1 + EPW);
             mbar_init(&b_empty[i], 1);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
+        *copy_issued = 0;
+        *copy_stopped = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -377,49 +392,51 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
     const int32_t s0 = static_cast<int32_t>(u0 - t0 * K);
     if (warp == 0) {
         // ------------------------------- copy warp -------------------------------------
-        if (lane == 0 && !A.stall) {
-            int64_t t = t0;
-            int32_t st = s0;
-            const uint8_t *bsrc = A.Bop + (t * TC_T + static_cast<int64_t>(st) * JS) * TC_ROW;
-            int64_t cur_t = -1;
-            uint32_t na = 0;
-            int32_t slot = 0;
-            uint32_t eph = 1;   // parity of the b_empty phase to wait for (first pass: free)
+        if (lane == 0) {
             int32_t q = 0;
-            for (; q < nu; ++q) {
-                if (t != cur_t) {
-                    const uint32_t as = na & 1u;
-                    if (!(TRYW ? mbar_sleep_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)
-                               : mbar_spin_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)))
-                        break;
-                    mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
-                    bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
-                    ++na;
-                    cur_t = t;
-                }
-                if (!(TRYW ? mbar_sleep_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)
-                           : mbar_spin_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)))
-                    break;
-                mbar_arrive_expect_tx(&b_full[slot], kStage);
-                bulk_g2s(sB + slot * kStage, bsrc, kStage, &b_full[slot]);
-                bsrc += JS * TC_ROW;
-                if (++st == K32) {
-                    st = 0;
-                    ++t;
-                    bsrc = A.Bop + t * TC_T * TC_ROW;
-                }
-                if (++slot == NS) {
-                    slot = 0;
-                    eph ^= 1u;
+            uint32_t na = 0;
+            if (!A.stall) {
+                int64_t t = t0;
+                int32_t st = s0;
+                const uint8_t *bsrc = A.Bop + (t * TC_T + static_cast<int64_t>(st) * JS) * TC_ROW;
+                int64_t cur_t = -1;
+                int32_t slot = 0;
+                uint32_t eph = 1;   // parity of the b_empty phase to wait for (first pass: free)
+                for (; q < nu; ++q) {
+                    if (t != cur_t) {
+                        const uint32_t as = na & 1u;
+                        if (!mbar_sleep_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
+                        mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
+                        bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
+                        ++na;
+                        cur_t = t;
+                    }
+                    if (!mbar_sleep_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)) break;
+                    mbar_arrive_expect_tx(&ready[slot], kStage);
+                    bulk_g2s(sB + slot * kStage, bsrc, kStage, &ready[slot]);
+                    bsrc += JS * TC_ROW;
+                    if (++st == K32) {
+                        st = 0;
+                        ++t;
+                        bsrc = A.Bop + t * TC_T * TC_ROW;
+                    }
+                    if (++slot == NS) {
+                        slot = 0;
+                        eph ^= 1u;
+                    }
                 }
             }
+            *copy_issued = q;
+            __threadfence_block();
+            *copy_stopped = 1;
             // Every copy issued above is waited for by the MMA lane before it retires the
             // slot; after an abort the MMA lane may have stopped early, so wait here
-            // (bounded) for the last copy of every slot and of both i-tile slots.
+            // (bounded) for the last copy of every slot (the epilogue warps make their
+            // remaining ready arrivals for these units) and of both i-tile slots.
             if (*abort_flag) {
                 const int32_t issued = q;
                 for (int32_t qq = issued > NS ? issued - NS : 0; qq < issued; ++qq)
-                    (void)mbar_wait_bounded(&b_full[qq % NS], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
+                    (void)mbar_wait_bounded(&ready[qq % NS], static_cast<uint32_t>((qq / NS) & 1), A.wait_ns);
                 for (uint32_t k = (na > 2 ? na - 2 : 0); k < na; ++k)
                     (void)mbar_wait_bounded(&a_full[k & 1u], (k >> 1) & 1u, A.wait_ns);
             }
@@ -436,12 +453,11 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             bool new_tile = true;
             uint32_t na = 0;
             int32_t slot = 0, buf = 0;
-            uint32_t fph = 0;   // b_full phase parity
-            uint32_t eph = 1;   // t_empty phase parity to wait for (first pass: free)
+            uint32_t rph = 0;   // ready phase parity
             bool ok = true;
-            // outcome of the next unit's two barrier tests, taken early (right after the
-            // previous MMA) so that their latency overlaps the commits
-            bool pre_full = false, pre_empty = false;
+            // outcome of the next unit's barrier test, taken early (right after the
+            // previous commit) so that its latency overlaps the MMA
+            bool pre_ready = false;
             for (int32_t q = 0; q < nu; ++q) {
                 if (new_tile) {
                     ok = mbar_spin_bounded(&a_full[na & 1u], (na >> 1) & 1u, A.wait_ns, abort_flag);
@@ -449,31 +465,20 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                     ++na;
                 }
                 const uint32_t as = (na - 1) & 1u;
-                ok = (pre_full || mbar_spin_bounded(&b_full[slot], fph, A.wait_ns, abort_flag)) &&
-                     (pre_empty || mbar_spin_bounded(&t_empty[buf], eph, A.wait_ns, abort_flag));
+                ok = pre_ready || mbar_spin_bounded(&ready[slot], rph, A.wait_ns, abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad0 + as * (TC_ATILE >> 4),
                             bd0 + static_cast<uint32_t>(slot) * (kStage >> 4), idesc, 0u);
-                const int32_t cslot = slot, cbuf = buf;
+                tc_commit(&t_full[buf]);
                 new_tile = ++st == K32;
                 if (new_tile) st = 0;
                 if (++slot == NS) {
                     slot = 0;
-                    fph ^= 1u;
+                    rph ^= 1u;
                 }
-                if (++buf == NB) {
-                    buf = 0;
-                    eph ^= 1u;
-                }
-                if (CF) tc_commit(&t_full[cbuf]);   // the epilogue's barrier first
-                if (PRE) {
-                    pre_full = mbar_test_wait(&b_full[slot], fph);
-                    pre_empty = mbar_test_wait(&t_empty[buf], eph);
-                }
-                if (!STEW) tc_commit(&b_empty[cslot]);
-                if (!CF) tc_commit(&t_full[cbuf]);
-                if (!STEW && (new_tile || q + 1 == nu)) tc_commit(&a_empty[as]);
+                if (++buf == NB) buf = 0;
+                pre_ready = mbar_test_wait(&ready[slot], rph);
             }
             if (!ok) {
                 flag_status(A.hdr, ST_TIMEOUT);
@@ -483,6 +488,34 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             tc_commit(done);
             if (!mbar_wait_bounded(done, 0u, A.wait_ns)) flag_status(A.hdr, ST_TIMEOUT);
         }
+    } else if (warp == 2 + EPW) {
+        // ------------------------------- slot-return warp ------------------------------
+        if (lane == 0) {
+            int32_t st = s0, buf = 0, rslot = 0;
+            uint32_t fph = 0, tord = 0;
+            for (int32_t q = 0; q < nu; ++q) {
+                if (!mbar_sleep_bounded(&t_full[buf], fph, A.wait_ns, abort_flag)) {
+                    if (!*abort_flag) {
+                        flag_status(A.hdr, ST_TIMEOUT);
+                        *abort_flag = 1;
+                    }
+                    break;
+                }
+                // unit q's MMA (and every earlier one) is complete: its j-stage slot, and
+                // after the share's last unit of a tile the i-tile slot, can be refilled
+                mbar_arrive(&b_empty[rslot]);
+                if (st == K32 - 1 || q + 1 == nu) mbar_arrive(&a_empty[tord & 1u]);
+                if (++buf == NB) {
+                    buf = 0;
+                    fph ^= 1u;
+                }
+                if (++rslot == NS) rslot = 0;
+                if (++st == K32) {
+                    st = 0;
+                    ++tord;
+                }
+            }
+        }
     } else {
         // ------------------------------- epilogue warps --------------------------------
         const int ew = warp - 2;
@@ -490,6 +523,9 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         const int part = ew >> 2;              // which CPW-column part of the accumulator
         const int row = quarter * 32 + lane;   // object offset inside the i-tile
         const uint32_t lane_addr = static_cast<uint32_t>(quarter * 32) << 16;
+        // the accumulators of the first NB units start free
+        if (lane == 0)
+            for (int i = 0; i < NB; ++i) mbar_arrive(&ready[i]);
         f2 acc[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
         unsigned long long cnt = 0;
         double sum = 0.0;
@@ -500,12 +536,11 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
         int32_t buf = 0;
         uint32_t fph = 0;   // t_full phase parity
         int32_t rslot = 0;  // j-stage ring slot of unit q
-        uint32_t tord = 0;  // ordinal of unit q's tile in this share (i-tile slot tord & 1)
-        for (int32_t q = 0; q < nu; ++q) {
+        int32_t q = 0;
+        for (; q < nu; ++q) {
             const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
-            const bool got = __all_sync(0xFFFFFFFFu, TRYW ? mbar_sleep_bounded(&t_full[buf], fph, A.wait_ns, abort_flag)
-                                                          : mbar_spin_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
+            const bool got = __all_sync(0xFFFFFFFFu, mbar_sleep_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
                     flag_status(A.hdr, ST_TIMEOUT);
@@ -513,49 +548,24 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 }
                 break;
             }
-            if (STEW && ew == 0 && lane == 0) {
-                // unit q's MMA (and every earlier one) is complete: its j-stage slot, and
-                // after the share's last unit of a tile the i-tile slot, can be refilled
-                mbar_arrive(&b_empty[rslot]);
-                if (st == K32 - 1 || q + 1 == nu) mbar_arrive(&a_empty[tord & 1u]);
-            }
+            // the ready barrier of the unit that overwrites this accumulator next
+            uint64_t *release = &ready[rslot + NB < NS ? rslot + NB : rslot + NB - NS];
             tc_fence_after();
             uint32_t v[CPW];
-            float vmin = -1.0f;   // RED: the minimum of this thread's values
-            if constexpr (RED) {
-                vmin = tmem_ld_min<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
-            } else {
-                tmem_ld<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
-            }
-            // RED: does any lane of the warp hold a negative value? (warp-uniform skip)
-            bool warp_neg = true;
-            if constexpr (RED && !WALK) warp_neg = __any_sync(0xFFFFFFFFu, vmin < 0.0f);
+            const float vmin = tmem_ld_min<CPW>(tbase + lane_addr + static_cast<uint32_t>(buf * JS + part * CPW), v);
+            // does any lane of the warp hold a negative value? (warp-uniform)
+            const bool warp_neg = __any_sync(0xFFFFFFFFu, vmin < 0.0f);
             if (!WALK) {
-                // the accumulator is in registers: hand the TMEM buffer back to the MMA lane
-                // before counting, so the next MMA overlaps this warp's arithmetic
+                // the accumulator is in registers: hand the TMEM buffer back before
+                // counting, so the next MMA into it overlaps this warp's arithmetic
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&t_empty[buf]);
+                if (lane == 0) mbar_arrive(release);
             }
             const bool full = eo0 >= TC_T && eo0 + JS - 1 <= A.h;
             if (WALK) {
-                // screen: any negative value in the warp's block of the accumulator? The
-                // rounding-down FMA of the count kernel on fresh accumulators (the FMA pipe
-                // measured faster here than an OR screen on the ALU pipe)
-                bool any_neg;
-                if constexpr (RED) {
-                    any_neg = __any_sync(0xFFFFFFFFu, vmin < 0.0f);
-                } else {
-                    f2 sa[4] = {kAccInit, kAccInit, kAccInit, kAccInit};
-#pragma unroll
-                    for (int j = 0; j < CPW / 2; ++j) {
-                        const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
-                        sa[j & 3] = f2_fma_rm(pv, kScale, sa[j & 3]);
-                    }
-                    any_neg = __any_sync(0xFFFFFFFFu, (sa[0] & sa[1] & sa[2] & sa[3]) != kAccInit);
-                }
-                if (any_neg) {
-                    // one bit per group of 8 columns holding one, warp-uniform
+                if (warp_neg) {
+                    // one bit per group of 8 columns holding a negative value, warp-uniform
                     uint32_t gm = 0;
 #pragma unroll
                     for (int g = 0; g < CPW / 8; ++g) {
@@ -574,7 +584,6 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                         zi = A.pz[io];
                         ri = A.pr[io];
                     }
-                    // walk the flagged groups exactly (compact code: one group at a time)
                     // columns c of this row that the schedule assigns: 1 <= d0 + c <= ev
                     int32_t clo = 0, cspan = CPW - 1;
                     if (!full) {
@@ -634,29 +643,15 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
                 // the walk is done with the accumulator: hand the TMEM buffer back
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&t_empty[buf]);
-            } else {
+                if (lane == 0) mbar_arrive(release);
+            } else if (warp_neg) {
                 if (full) {
-                    constexpr int NF = CPW - SCR;   // values counted on the FP32 pipe
-                    static_assert(SCR % 2 == 0 && NF % 8 == 0, "split of the values");
-                    // RED: only warps holding a negative value count
-                    if (warp_neg) {
 #pragma unroll
-                        for (int j = 0; j < NF / 2; ++j) {
-                            const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
-                            acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
-                        }
+                    for (int j = 0; j < CPW / 2; ++j) {
+                        const f2 pv = static_cast<f2>(v[2 * j]) | (static_cast<f2>(v[2 * j + 1]) << 32);
+                        acc[j & 3] = f2_fma_rm(pv, kScale, acc[j & 3]);
                     }
-                    if constexpr (SCR > 0) {
-                        uint32_t orv = 0;
-#pragma unroll
-                        for (int j = NF; j < CPW; j += 2) orv |= v[j] | v[j + 1];
-                        if (orv & 0x80000000u) {   // a negative value (or -0) among them
-#pragma unroll
-                            for (int j = NF; j < CPW; ++j) cnt += __uint_as_float(v[j]) < 0.0f ? 1u : 0u;
-                        }
-                    }
-                } else if (warp_neg) {
+                } else {
                     const int64_t i = t * TC_T + row;
                     const int64_t ev = i < A.n ? A.h + (((A.n & 1) == 0 && i < A.n / 2) ? 1 : 0) : -1;
                     const int64_t d0 = static_cast<int64_t>(eo0) + part * CPW - row;   // e - i of column 0
@@ -680,8 +675,33 @@ __global__ void __launch_bounds__((2 + EPW) * 32, 1) k_pairs_tc(TcArgs A) {
             if (++st == K32) {
                 st = 0;
                 ++t;
-                ++tord;
             }
+        }
+        if (q < nu) {
+            // Aborted at unit q (not released). The copy warp drains the stage copies it
+            // issued by waiting for their ready phases, which also need this warp's
+            // releases: make them (units q + NB .. issued - 1) in order, each after the
+            // previous phase of its slot completed, so that no arrival lands in the wrong
+            // phase. Every wait is bounded.
+            const uint64_t t_stop = globaltimer_ns();
+            bool have = true;
+            while (!*copy_stopped) {
+                if (globaltimer_ns() - t_stop > A.wait_ns) {
+                    have = false;
+                    break;
+                }
+            }
+            __syncwarp();
+            if (have && lane == 0) {
+                const int32_t issued = *copy_issued;
+                for (int32_t u = q + NB; u < issued; ++u) {
+                    if (u >= NS &&
+                        !mbar_wait_bounded(&ready[u % NS], static_cast<uint32_t>(((u - NS) / NS) & 1), A.wait_ns))
+                        break;
+                    mbar_arrive(&ready[u % NS]);
+                }
+            }
+            __syncwarp();
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) cnt += acc_count(acc[a]);
@@ -755,43 +775,33 @@ struct TcLaunch {
     int js, threads;
 };
 
-template <int JS, int NB, int EPW, int NS, int SCR = 0, bool PRE = false, bool STEW = false, bool SUMT = false,
-          bool SPH = false, bool RED = false, bool WALKC = false, bool TRYW = false, bool CF = false>
+template <bool SUMT, bool SPH, bool WALKC>
 static cc_status tc_launch_of(TcLaunch &L) {
-    static_assert(TcSmem<JS, NB, EPW, NS>::kTotal <= TC_SMEM_REQ, "shared memory layout");
-    auto fn = k_pairs_tc<JS, NB, EPW, NS, SCR, PRE, STEW, SUMT, SPH, RED, WALKC, TRYW, CF>;
+    static_assert(TcSmem::kTotal <= TC_SMEM_REQ, "shared memory layout");
+    auto fn = k_pairs_tc<SUMT, SPH, WALKC>;
     // shared-memory attribute, once per instance (thread-safe static initialisation)
     static const cudaError_t attr =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQ);
     CC_CUDA(attr);
     L.fn = reinterpret_cast<const void *>(fn);
-    L.js = JS;
-    L.threads = (2 + EPW) * 32;
+    L.js = TC_JS;
+    L.threads = TC_THREADS;
     return CC_OK;
 }
 
-// The compiled shapes, all 256-object stages (MMA N), two 256-column accumulators, eight
-// epilogue warps, a 12-deep j-stage ring, early barrier tests, epilogue slot returns,
-// min-reducing TMEM loads, sleeping waits in the epilogue and copy warps and the
-// accumulator's commit before the early tests (template arguments: JS, NB, EPW, NS, SCR,
-// PRE, STEW, SUMT, SPH, RED, WALKC, TRYW, CF). They differ in the epilogue: the integer
-// count in registers (dense hits) or by the walk (sparse hits), the integer interaction
-// sum, and the FP32 sphere count and sum (walks behind the integer screen). The
-// alternatives measured slower on GB300 are listed with their rates in the design notes.
+// The compiled epilogue forms: the integer count in registers (dense hits) or by the walk
+// (sparse hits), the integer interaction sum, and the FP32 sphere count and sum (walks
+// behind the integer screen). The alternatives measured slower on GB300 are listed with
+// their rates in the design notes.
 enum class TcForm { CountRegisters, CountWalk, Sum, SphereCount, SphereSum };
 
 static cc_status tc_form_launch(TcLaunch &L, TcForm f) {
     switch (f) {
-        case TcForm::CountRegisters:
-            return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, false, true, true>(L);
-        case TcForm::CountWalk:
-            return tc_launch_of<256, 2, 8, 12, 0, true, true, false, false, true, true, true, true>(L);
-        case TcForm::Sum:
-            return tc_launch_of<256, 2, 8, 12, 0, true, true, true, false, true, false, true, true>(L);
-        case TcForm::SphereCount:
-            return tc_launch_of<256, 2, 8, 12, 0, true, true, false, true, true, false, true, true>(L);
-        default:
-            return tc_launch_of<256, 2, 8, 12, 0, true, true, true, true, true, false, true, true>(L);
+        case TcForm::CountRegisters: return tc_launch_of<false, false, false>(L);
+        case TcForm::CountWalk: return tc_launch_of<false, false, true>(L);
+        case TcForm::Sum: return tc_launch_of<true, false, false>(L);
+        case TcForm::SphereCount: return tc_launch_of<false, true, false>(L);
+        default: return tc_launch_of<true, true, false>(L);
     }
 }
 
