@@ -13,6 +13,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -41,6 +42,11 @@ bool tc_enabled();
 // Sets at least this large have their count and sum queries served by the single-set
 // path (a tensor-core kernel when the set admits it) instead of the batch.
 constexpr int64_t kServerTcMinN = 16384;
+// Batches of at most this many requests, all on sets below the single-set path's small-set
+// limit, skip the batching graph: each request is one launch of the small-set kernel,
+// which for so few requests is sooner done than the graph's six kernels.
+constexpr size_t kDirectMaxRequests = 4;
+int64_t tc_min_n();
 void *plan_sets_buffer_v(cc_plan *P);
 size_t plan_set_desc_bytes();
 
@@ -102,6 +108,7 @@ struct cc_server {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Req> pending;
+    std::atomic<int64_t> npending{0};   // pending.size(), readable without the lock
     std::vector<SetRec> sets;
     size_t resident_bytes = 0;
     size_t inflight_bytes = 0;
@@ -205,8 +212,12 @@ static bool launch(cc_server *S, Lane &L) {
             scratch += q.scratch;
             points += n;
             S->pending.pop_front();
+            S->npending.fetch_sub(1);
         }
         if (batch.empty()) return false;
+        // a few requests on small sets: one small-set kernel launch each, no graph
+        bool direct = batch.size() <= kDirectMaxRequests;
+        for (size_t k = 0; direct && k < batch.size(); ++k) direct = S->sets[batch[k].set_id].n < tc_min_n();
         S->inflight += static_cast<int64_t>(batch.size());
         S->inflight_bytes += scratch;
         S->admitted += static_cast<int64_t>(batch.size());
@@ -225,7 +236,7 @@ static bool launch(cc_server *S, Lane &L) {
             d.n = sr.n;
             d.dtype = sr.dtype;
             d.r2 = batch[k].r2;
-            if (sr.single) {
+            if (sr.single || direct) {
                 cc_points pts;
                 pts.dtype = sr.dtype;
                 pts.x = d.x;
@@ -246,10 +257,14 @@ static bool launch(cc_server *S, Lane &L) {
     L.scratch = scratch;
     L.busy = true;
     const int32_t nb = static_cast<int32_t>(L.batch.size());
-    cudaError_t e = cudaMemcpyAsync(plan_sets_buffer_v(L.plan), L.h_sets, sizeof(SetDescHost) * nb,
-                                    cudaMemcpyHostToDevice, L.stream);
-    cc_status st = e == cudaSuccess ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
-                                    : CC_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    cc_status st = CC_OK;
+    if (L.singles.size() < L.batch.size()) {   // some entries run in the batching graph
+        e = cudaMemcpyAsync(plan_sets_buffer_v(L.plan), L.h_sets, sizeof(SetDescHost) * nb, cudaMemcpyHostToDevice,
+                            L.stream);
+        st = e == cudaSuccess ? plan_launch_sets(L.plan, nb, any_sum ? 1 : 0, L.d_counts, L.d_sums, L.stream)
+                              : CC_ERR_CUDA;
+    }
     // queries on large sets: one single-set call each, stream-ordered after the batch
     // (this thread is the lane stream's only user, so its workspace is too)
     for (size_t j = 0; st == CC_OK && j < L.singles.size(); ++j) {
@@ -275,6 +290,10 @@ static bool launch(cc_server *S, Lane &L) {
     return true;
 }
 
+// The scheduler thread. While a lane's batch runs it polls the lanes' completion events
+// (and, with a lane idle, the request queue) without sleeping for up to 200 us, so that a
+// finished batch is harvested and a new request launched within a few microseconds; it
+// sleeps on the condition variable only after that, or when nothing is in flight.
 static void scheduler(cc_server *S) {
     cudaSetDevice(S->device);
     for (;;) {
@@ -288,17 +307,26 @@ static void scheduler(cc_server *S) {
         for (Lane &L : S->lanes) {
             if (!L.busy && launch(S, L)) progressed = true;
         }
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            if (S->stop && S->pending.empty() && S->inflight == 0) return;
-            if (!progressed) {
-                const bool any_busy = S->lanes[0].busy || S->lanes[1].busy;
-                if (!any_busy && S->pending.empty() && !S->stop)
-                    S->cv.wait_for(lk, std::chrono::milliseconds(2));
-                else
+        if (progressed) continue;
+        if (S->lanes[0].busy || S->lanes[1].busy) {
+            const bool idle_lane = !S->lanes[0].busy || !S->lanes[1].busy;
+            const auto t0 = std::chrono::steady_clock::now();
+            for (;;) {
+                bool done = false;
+                for (Lane &L : S->lanes) done = done || (L.busy && cudaEventQuery(L.done) == cudaSuccess);
+                if (done || (idle_lane && S->npending.load() > 0)) break;
+                if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200)) {
+                    std::unique_lock<std::mutex> lk(S->mu);
                     S->cv.wait_for(lk, std::chrono::microseconds(20));
+                    break;
+                }
+                std::this_thread::yield();
             }
+            continue;
         }
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->stop && S->pending.empty() && S->inflight == 0) return;
+        if (S->pending.empty() && !S->stop) S->cv.wait_for(lk, std::chrono::milliseconds(2));
     }
 }
 
@@ -433,6 +461,7 @@ cc_status cc_server_submit(cc_server *S, int32_t set_id, int32_t op, uint32_t r2
     SetRec &r = S->sets[set_id];
     r.refs += 1;
     S->pending.push_back(Req{req_id, set_id, op, r2, t, req_scratch(r.n)});
+    S->npending.fetch_add(1);
     S->submitted += 1;
     S->cv.notify_all();
     return CC_OK;
