@@ -304,17 +304,26 @@ static void scheduler(cc_server *S) {
                 progressed = true;
             }
         }
+        bool tried = false;   // a launch was attempted and admitted nothing
         for (Lane &L : S->lanes) {
-            if (!L.busy && launch(S, L)) progressed = true;
+            if (!L.busy) {
+                if (launch(S, L)) progressed = true;
+                else tried = true;
+            }
         }
         if (progressed) continue;
         if (S->lanes[0].busy || S->lanes[1].busy) {
+            // with a lane idle, a new request is worth a launch attempt, unless the one just
+            // made admitted nothing (slots or budget exhausted): then only a finishing batch
+            // changes anything, and polling the queue would contend for the lock
+            const int64_t seen = S->npending.load();
             const bool idle_lane = !S->lanes[0].busy || !S->lanes[1].busy;
             const auto t0 = std::chrono::steady_clock::now();
             for (;;) {
                 bool done = false;
                 for (Lane &L : S->lanes) done = done || (L.busy && cudaEventQuery(L.done) == cudaSuccess);
-                if (done || (idle_lane && S->npending.load() > 0)) break;
+                const int64_t np = S->npending.load();
+                if (done || (idle_lane && np > 0 && (!tried || np > seen))) break;
                 if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200)) {
                     std::unique_lock<std::mutex> lk(S->mu);
                     S->cv.wait_for(lk, std::chrono::microseconds(20));

@@ -276,3 +276,31 @@ def test_switch_between_kernels_gives_equal_counts(cc, r2):
     finally:
         cc.set_tensor_cores(True)
     assert a == b == oracle.count_i32(c["x"], c["y"], c["z"], r2)
+
+
+def test_two_streams_interleaved_stress(cc):
+    """Tensor-core counts and sums on two streams at once, interleaved with small-set
+    calls, many times over: every result exact and no device-side wait runs out (a stall
+    anywhere in a kernel's pipeline would surface as CC_ERR_TIMEOUT after the wait bound)."""
+    rng = np.random.default_rng(41)
+    big = [box_points(rng, n, 1023) for n in (9001, 20000, 40001)]
+    want = [oracle.count_i32(*b, 9) for b in big]
+    small = box_points(rng, 3000, 40)
+    want_small = oracle.count_i32(*small, 9)
+    tb = [dev(*b) for b in big]
+    ts = dev(*small)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for rep in range(40):
+        for k, s in enumerate(streams):
+            with torch.cuda.stream(s):
+                j = (rep + k) % 3
+                outs.append((cc.count_pairs(*tb[j], r2=9, stream=s), want[j]))
+                outs.append((cc.count_pairs(*ts, r2=9, stream=s), want_small))
+                if rep % 8 == k:
+                    sm, c = cc.interaction_sum(*tb[j], r2=9, stream=s)
+                    outs.append((c, want[j]))
+    torch.cuda.synchronize()
+    for s in streams:
+        assert cc.stream_status(s) == cc.CC_OK
+    assert [cc.as_u64(o) for o, _ in outs] == [w for _, w in outs]
