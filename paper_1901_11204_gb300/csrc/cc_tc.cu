@@ -235,6 +235,9 @@ constexpr int TC_CPW = TC_JS / (TC_EPW / 4);   // accumulator columns per epilog
 constexpr int TC_THREADS = (2 + TC_EPW) * 32;
 static_assert(TC_NB * TC_JS == 512, "the accumulators fill the 512 TMEM columns");
 static_assert(TC_NS > TC_NB, "a unit's stage slot outlives the release of its accumulator");
+// Least number of stages per i-tile the pipeline needs (the i-tile slots are freed through
+// the stage waits): n >= 6144 objects gives K = ceil((128 + (n-1)/2 + 1) / 256) >= 13.
+constexpr int TC_MIN_K = TC_NS + 1;
 
 struct TcSmem {
     static constexpr int kStage = TC_JS * TC_ROW;         // bytes of one j-stage
@@ -312,9 +315,9 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // kernel chose it (hdr->tc_form, from the expected hit density; TcArgs::form).
 //
 // Barriers (mbarrier, shared memory):
-//   a_full[2]          i-tile slots: copied by warp 0 (the copy lane reuses a slot once the
-//                      ready phase of the unit two after the slot's previous tile's last
-//                      unit completed: then that tile's last MMA has completed);
+//   a_full[2]          i-tile slots, copied by warp 0. A slot is reused for the tile two
+//                      after its previous one; every tile spans at least TC_MIN_K units, so
+//                      by then the stage waits below have seen that tile's last MMA complete;
 //   ready[NS]          unit q may run: the stage copy of q landed (the copy warp's
 //                      arrive.expect_tx and the copy's bytes) AND every epilogue warp
 //                      released the accumulator unit q will overwrite (the one of unit
@@ -400,29 +403,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
                 const uint8_t *bsrc = A.Bop + (t * TC_T + static_cast<int64_t>(st) * JS) * TC_ROW;
                 int64_t cur_t = -1;
                 int32_t slot = 0;
-                int32_t last_even = -1, last_odd = -1;   // last unit of the latest tiles by ordinal parity
                 for (; q < nu; ++q) {
                     if (t != cur_t) {
+                        // The i-tile slot's previous tile (two tiles before) is done: every
+                        // tile spans at least NS + 1 units (TC_MIN_K), so before this unit the
+                        // stage wait below already saw the MMA of unit q - 1 - NS complete,
+                        // which is after that tile's last MMA.
                         const uint32_t as = na & 1u;
-                        if (na >= 1) {
-                            if ((na - 1) & 1u) last_odd = q - 1;
-                            else last_even = q - 1;
-                        }
-                        if (na >= 2) {
-                            // the tile two before left this slot: its last MMA completed once the
-                            // ready phase two units after that MMA completed
-                            const int32_t u = (as ? last_odd : last_even) + NB;
-                            if (!mbar_sleep_bounded(&ready[u % NS], static_cast<uint32_t>((u / NS) & 1), A.wait_ns,
-                                                    abort_flag))
-                                break;
-                        }
                         mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
                         bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
                         ++na;
                         cur_t = t;
                     }
                     if (q >= NS) {
-                        // unit q - NS, the slot's previous user, has completed its MMA
+                        // unit q - NS, the slot's previous user, has completed its MMA. The
+                        // barrier watched cannot move past this phase before this lane issues
+                        // the copy of unit u + NS = q + NB, so a parity wait cannot alias.
                         const int32_t u = q - NS + NB;
                         if (!mbar_sleep_bounded(&ready[u % NS], static_cast<uint32_t>((u / NS) & 1), A.wait_ns,
                                                 abort_flag))
@@ -823,6 +819,7 @@ cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region,
                                          : (sum ? TcForm::Sum : TcForm::CountRegisters));
     if (st != CC_OK) return st;
     const TcGeom g = tc_geometry(n, L.js);
+    if (g.K < TC_MIN_K) return fail(CC_ERR_INVALID_ARG, "set too small for the tensor-core kernel");
     TcArgs A;
     A.Aop = region;
     A.Bop = region + g.a_bytes;
