@@ -48,12 +48,12 @@ cc_status tc_enqueue_pairs(const cc_points *p, int64_t n, const uint8_t *region,
 // tensor-core and FP32-pipe forms: at 8192 both take about 33 us per call, at 12288 the
 // tensor cores 25-30 % less), or the environment variable CC_TC_MIN_N (read once).
 int64_t tc_min_n() {
-    // at least 6144: the tensor-core kernel's pipeline needs every i-tile to span at least
-    // 13 of its units (TC_MIN_K)
+    // at least 1024: the tensor-core kernel's pipeline needs every i-tile to span at least
+    // two of its units (TC_MIN_K; true from n = 257 on)
     static const int64_t v = []() {
         const char *e = getenv("CC_TC_MIN_N");
         const int64_t want = e ? static_cast<int64_t>(atoll(e)) : int64_t{8192};
-        return want >= 6144 ? want : int64_t{6144};
+        return want >= 1024 ? want : int64_t{1024};
     }();
     return v;
 }

@@ -231,21 +231,22 @@ constexpr int TC_EPW = 8;
 constexpr int TC_NS = 12;
 constexpr int TC_CPW = TC_JS / (TC_EPW / 4);   // accumulator columns per epilogue warp and unit
 // warps: copy, MMA, TC_EPW epilogue warps (warps 2 .. 2 + TC_EPW - 1, so that warp & 3 is the
-// TMEM lane quarter each may read)
-constexpr int TC_THREADS = (2 + TC_EPW) * 32;
+// TMEM lane quarter each may read), and one slot-return warp
+constexpr int TC_THREADS = (3 + TC_EPW) * 32;
 static_assert(TC_NB * TC_JS == 512, "the accumulators fill the 512 TMEM columns");
 static_assert(TC_NS > TC_NB, "a unit's stage slot outlives the release of its accumulator");
-// Least number of stages per i-tile the pipeline needs (the i-tile slots are freed through
-// the stage waits): n >= 6144 objects gives K = ceil((128 + (n-1)/2 + 1) / 256) >= 13.
-constexpr int TC_MIN_K = TC_NS + 1;
+// Least number of stages (units) per i-tile: the slot-return warp frees an i-tile slot once
+// the ready phase two units after the tile's last unit completed, and that unit's copy must
+// come before the tile two later's (true for n >= 257 objects; the path starts far above).
+constexpr int TC_MIN_K = 2;
 
 struct TcSmem {
     static constexpr int kStage = TC_JS * TC_ROW;         // bytes of one j-stage
     static constexpr int kA = 0;                          // 2 i-tile slots
     static constexpr int kB = 2 * TC_ATILE;               // TC_NS j-stage slots
     static constexpr int kBars = kB + TC_NS * kStage;
-    // a_full[2] ready[NS] t_full[NB] done
-    static constexpr int kNBars = 3 + TC_NS + TC_NB;
+    // a_full[2] a_empty[2] ready[NS] b_empty[NS] t_full[NB] done
+    static constexpr int kNBars = 5 + 2 * TC_NS + TC_NB;
     static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag, copy drain words
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
     static constexpr int kRedSum = kRed + TC_EPW * 8;     // per-epilogue-warp sums
@@ -315,24 +316,27 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // kernel chose it (hdr->tc_form, from the expected hit density; TcArgs::form).
 //
 // Barriers (mbarrier, shared memory):
-//   a_full[2]          i-tile slots, copied by warp 0. A slot is reused for the tile two
-//                      after its previous one; every tile spans at least TC_MIN_K units, so
-//                      by then the stage waits below have seen that tile's last MMA complete;
+//   a_full/a_empty[2]  i-tile slots: copied by warp 0, freed by the slot-return warp
+//                      once the tile's last MMA of this CTA completed (seen as below);
 //   ready[NS]          unit q may run: the stage copy of q landed (the copy warp's
 //                      arrive.expect_tx and the copy's bytes) AND every epilogue warp
 //                      released the accumulator unit q will overwrite (the one of unit
 //                      q - NB; arrive count 1 + EPW, the first NB units pre-arrived), so
 //                      that the MMA thread, the pipeline's critical path, tests one
 //                      barrier per unit;
-//                      The copy lane also learns from ready that a stage slot is free: the
-//                      phase of unit q + 2 completes only once every epilogue warp released
-//                      unit q's accumulator, so unit q's MMA (the last reader of the slot)
-//                      has completed. (A separate slot-return warp watching t_full by phase
-//                      parity could lag far enough for its parity to alias onto a phase that
-//                      waits for the very slot it holds; the copy lane cannot lag, because it
-//                      itself gates the next phase of the barrier it watches. No epilogue
-//                      warp returns slots: with that duty one warp trailed the others by
-//                      about 300 cycles per unit and paced the pipeline.)
+//   b_empty[NS]        stage slot free again: the slot-return warp, once unit q's MMA
+//                      completed, which it sees as the completion of the ready phase of
+//                      unit q + NB (that phase needs every epilogue warp's release of unit
+//                      q's accumulator, read after the MMA completed). The warp watches these
+//                      phases in unit order, and the next phase of the barrier it watches
+//                      (unit q + NB + NS) needs the copy into the very slot it frees only
+//                      later, so it can never fall a phase behind and misread a parity
+//                      (watching t_full instead, a lagging warp could). It is a warp of its
+//                      own so that the epilogue warps, all of which must release an
+//                      accumulator before the next MMA into it, do equal work: an epilogue
+//                      warp with this extra duty trailed the others by about 300 cycles per
+//                      unit and paced the pipeline. The slots of the share's last NB units
+//                      are never needed again and are not returned;
 //   t_full[NB]         accumulator written: tcgen05.commit after the unit's MMA;
 //   done               every MMA of this CTA completed (before TMEM is freed).
 template <bool SUMT, bool SPH, bool WALKC>
@@ -349,9 +353,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
     uint8_t *sA = smem + L::kA;
     uint8_t *sB = smem + L::kB;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBars);
-    uint64_t *a_full = bars;
-    uint64_t *ready = bars + 2;
-    uint64_t *t_full = ready + NS, *done = t_full + NB;
+    uint64_t *a_full = bars, *a_empty = bars + 2;
+    uint64_t *ready = bars + 4, *b_empty = bars + 4 + NS;
+    uint64_t *t_full = bars + 4 + 2 * NS, *done = t_full + NB;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
     // the copy warp's number of issued stage copies, published when it stops (drain)
@@ -362,9 +366,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) mbar_init(&a_full[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+        }
         for (int i = 0; i < NB; ++i) mbar_init(&t_full[i], 1);
-        for (int i = 0; i < NS; ++i) mbar_init(&ready[i], 1 + EPW);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&ready[i], 1 + EPW);
+            mbar_init(&b_empty[i], 1);
+        }
         mbar_init(done, 1);
         *abort_flag = 0;
         *copy_issued = 0;
@@ -403,27 +413,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
                 const uint8_t *bsrc = A.Bop + (t * TC_T + static_cast<int64_t>(st) * JS) * TC_ROW;
                 int64_t cur_t = -1;
                 int32_t slot = 0;
+                uint32_t eph = 1;   // parity of the b_empty phase to wait for (first pass: free)
                 for (; q < nu; ++q) {
                     if (t != cur_t) {
-                        // The i-tile slot's previous tile (two tiles before) is done: every
-                        // tile spans at least NS + 1 units (TC_MIN_K), so before this unit the
-                        // stage wait below already saw the MMA of unit q - 1 - NS complete,
-                        // which is after that tile's last MMA.
                         const uint32_t as = na & 1u;
+                        if (!mbar_sleep_bounded(&a_empty[as], ((na >> 1) & 1u) ^ 1u, A.wait_ns, abort_flag)) break;
                         mbar_arrive_expect_tx(&a_full[as], TC_ATILE);
                         bulk_g2s(sA + as * TC_ATILE, A.Aop + t * TC_ATILE, TC_ATILE, &a_full[as]);
                         ++na;
                         cur_t = t;
                     }
-                    if (q >= NS) {
-                        // unit q - NS, the slot's previous user, has completed its MMA. The
-                        // barrier watched cannot move past this phase before this lane issues
-                        // the copy of unit u + NS = q + NB, so a parity wait cannot alias.
-                        const int32_t u = q - NS + NB;
-                        if (!mbar_sleep_bounded(&ready[u % NS], static_cast<uint32_t>((u / NS) & 1), A.wait_ns,
-                                                abort_flag))
-                            break;
-                    }
+                    if (!mbar_sleep_bounded(&b_empty[slot], eph, A.wait_ns, abort_flag)) break;
                     mbar_arrive_expect_tx(&ready[slot], kStage);
                     bulk_g2s(sB + slot * kStage, bsrc, kStage, &ready[slot]);
                     bsrc += JS * TC_ROW;
@@ -432,7 +432,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
                         ++t;
                         bsrc = A.Bop + t * TC_T * TC_ROW;
                     }
-                    if (++slot == NS) slot = 0;
+                    if (++slot == NS) {
+                        slot = 0;
+                        eph ^= 1u;
+                    }
                 }
             }
             *copy_issued = q;
@@ -496,6 +499,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
             // all MMAs issued by this thread complete before TMEM is freed
             tc_commit(done);
             if (!mbar_wait_bounded(done, 0u, A.wait_ns)) flag_status(A.hdr, ST_TIMEOUT);
+        }
+    } else if (warp == 2 + EPW) {
+        // ------------------------------- slot-return warp ------------------------------
+        if (lane == 0) {
+            int32_t st = s0, buf = 0, rslot = 0;
+            uint32_t fph = 0, tord = 0;
+            for (int32_t q = 0; q + NB < nu; ++q) {
+                const int32_t u = q + NB;
+                if (!mbar_sleep_bounded(&ready[u % NS], static_cast<uint32_t>((u / NS) & 1), A.wait_ns, abort_flag)) {
+                    if (!*abort_flag) {
+                        flag_status(A.hdr, ST_TIMEOUT);
+                        *abort_flag = 1;
+                    }
+                    break;
+                }
+                // unit q's MMA (and every earlier one) is complete: its j-stage slot, and
+                // after a tile's last unit the i-tile slot, can be refilled
+                mbar_arrive(&b_empty[rslot]);
+                if (st == K32 - 1) mbar_arrive(&a_empty[tord & 1u]);
+                if (++buf == NB) {
+                    buf = 0;
+                    fph ^= 1u;
+                }
+                if (++rslot == NS) rslot = 0;
+                if (++st == K32) {
+                    st = 0;
+                    ++tord;
+                }
+            }
         }
     } else {
         // ------------------------------- epilogue warps --------------------------------
