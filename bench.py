@@ -237,7 +237,13 @@ def roofline_peak_int(sms: int, mhz: float) -> float:
 
 # Tensor-core form: one TF32 contraction of K = 8 terms per pair test (16 flops).
 TC_FLOPS_PER_PAIR = 16
-TMEM_READ_BYTES_PER_CLK = 350   # measured TMEM->register rate per SM, eight warps of 16 KB loads
+# Hardware rates of the tensor-core kernel's own instruction shapes, measured on GB300 with
+# python -m paper_1901_11204_gb300.microbench (summary in profiles/): TMEM->register reads
+# with eight warps of tcgen05.ld.red.32x32b.x128.min per SM, and back-to-back
+# tcgen05.mma kind::tf32 M=128 N=256 K=8 (32768 pair tests each).
+TMEM_READ_BYTES_PER_CLK = 870
+MMA_CLK_PER_UNIT = 128.2
+PAIRS_PER_UNIT = 128 * 256
 # TF32 / BF16 dense tensor throughput ratio of the part's nominal figures (1.1 / 2.25 PF).
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -362,14 +368,24 @@ def main():
             "timing_note": "events bracket the tensor-core launch and the FP32-pipe launch that "
                            "returns at once in tensor mode",
         }
-        # The accumulator of every pair test is read back from TMEM (4 B per pair): the
-        # read rate measured on this GPU with the kernel's load shape is the tighter bound.
+        # The kernel's own hardware bounds: every pair test's accumulator is read back from
+        # TMEM (4 B per pair), and one MMA evaluates 32768 pair tests. Both measured on this
+        # GPU with the kernel's instruction shapes; the kernel runs well below either (its
+        # period is set by the latency of the accumulator hand-over chain).
         tmem_peak = sms * TMEM_READ_BYTES_PER_CLK * fmax * 1e6 / 4.0 / 1e9   # G pair tests/s
         roofline["tmem_read_bound"] = {
             "peak_pair_tests_per_s": tmem_peak,
             "frac": (pair_rate / tmem_peak) if pair_rate else None,
-            "basis": (f"{TMEM_READ_BYTES_PER_CLK} B/clk/SM TMEM-to-register reads measured with eight warps of "
-                      f"32x32b.x128 loads, x {sms} SMs x {fmax:.0f} MHz, 4 B of accumulator per pair test"),
+            "basis": (f"{TMEM_READ_BYTES_PER_CLK} B/clk/SM TMEM-to-register reads (eight warps of "
+                      f"tcgen05.ld.red.32x32b.x128.min, measured) x {sms} SMs x {fmax:.0f} MHz, "
+                      "4 B of accumulator per pair test"),
+        }
+        mma_peak = sms * PAIRS_PER_UNIT / MMA_CLK_PER_UNIT * fmax * 1e6 / 1e9
+        roofline["mma_issue_bound"] = {
+            "peak_pair_tests_per_s": mma_peak,
+            "frac": (pair_rate / mma_peak) if pair_rate else None,
+            "basis": (f"one tcgen05.mma kind::tf32 128x256x8 (32768 pair tests) every {MMA_CLK_PER_UNIT} SM "
+                      f"clocks (measured back to back) x {sms} SMs x {fmax:.0f} MHz"),
         }
     else:
         traffic, traffic_note = measured_traffic("fp32")
