@@ -269,6 +269,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip f32/batched/serving/cpu legs")
     ap.add_argument("--serving-queries", type=int, default=50000)
+    ap.add_argument("--leg", choices=["config1", "batched", "batched_plan", "f32_spheres", "i32_sums"],
+                    help="run only this secondary leg and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -290,6 +292,18 @@ def main():
     cc.build()
     cc.lib()
     stream = torch.cuda.current_stream()
+    if args.leg:
+        props = torch.cuda.get_device_properties(dev)
+        peaks, peak_src = load_peaks()
+        fmax = float(peaks.get("sm_max_mhz", 2070.0))
+        sms = props.multi_processor_count
+        legs = {"config1": lambda: bench_config1(cc, torch, dev, sms, fmax),
+                "batched": lambda: bench_batched(cc, torch, dev),
+                "batched_plan": lambda: bench_batched(cc, torch, dev, with_plain=False),
+                "f32_spheres": lambda: bench_f32(cc, torch, dev, sms, fmax, peak_src, peaks),
+                "i32_sums": lambda: bench_i32_sums(cc, torch, dev)}
+        print(json.dumps({"leg": args.leg, **legs[args.leg]()}), flush=True)
+        return 0
 
     sets = step_inputs(rank)
     tests_per_step = sum(pairs(len(s[0])) for s in sets)
@@ -731,7 +745,7 @@ def bench_schedules(cc, torch, dev, n=600_000):
             "paper": "1.12x on a Tesla P100 (Section 5), context only"}
 
 
-def bench_batched(cc, torch, dev):
+def bench_batched(cc, torch, dev, with_plain=True):
     c = synth.cfg4()
     off = c["offsets"]
     S = len(off) - 1
@@ -748,6 +762,10 @@ def bench_batched(cc, torch, dev):
     items = plan.last_items()
     n = np.diff(off)
     tests = int((n * (n - 1) // 2).sum())
+    if not with_plain:
+        plan.close()
+        return {"workload": f"{S} pruned sets, {int(off[-1])} int32 points, r2={c['r2']}", "ms": ms,
+                "sets_per_s": S / (ms * 1e-3), "gpairs_s": tests / (ms * 1e-3) / 1e9, "work_items": items}
     # plain per-set launches on the same GPU, every set: cc_count_pairs per set, which for
     # sets below 8192 objects is one launch of the small-set kernel (the same stage loop,
     # no preparation pass), and the tensor-core path for the one set of 8192
