@@ -119,7 +119,20 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
         mn[a] = __reduce_min_sync(0xFFFFFFFFu, mn[a]);
         mx[a] = __reduce_max_sync(0xFFFFFFFFu, mx[a]);
     }
-    if ((threadIdx.x & 31) == 0) {
+    // one set of global atomics per block (per-warp atomics on the same six words serialise)
+    __shared__ uint32_t wred[32][6];
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            wred[threadIdx.x >> 5][a] = mn[a];
+            wred[threadIdx.x >> 5][3 + a] = mx[a];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w)
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = min(mn[a], wred[w][a]);
+                mx[a] = max(mx[a], wred[w][3 + a]);
+            }
         for (int a = 0; a < 3; ++a) {
             atomicMin(&h->umin[a], mn[a]);
             atomicMax(&h->umax[a], mx[a]);
@@ -223,7 +236,26 @@ __global__ void k_minmax_f32(const float *__restrict__ x, const float *__restric
     }
     rmax = __reduce_max_sync(0xFFFFFFFFu, rmax);
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+    // one set of global atomics per block (per-warp atomics on the same words serialise)
+    __shared__ uint32_t wred[32][8];
     if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            wred[threadIdx.x >> 5][a] = mn[a];
+            wred[threadIdx.x >> 5][3 + a] = mx[a];
+        }
+        wred[threadIdx.x >> 5][6] = rmax;
+        wred[threadIdx.x >> 5][7] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = min(mn[a], wred[w][a]);
+                mx[a] = max(mx[a], wred[w][3 + a]);
+            }
+            rmax = max(rmax, wred[w][6]);
+            bad |= wred[w][7];
+        }
         for (int a = 0; a < 3; ++a) {
             atomicMin(&h->umin[a], mn[a]);
             atomicMax(&h->umax[a], mx[a]);
@@ -281,7 +313,7 @@ __global__ void k_fill_i32(const int32_t *__restrict__ x, const int32_t *__restr
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
             int64_t e = 2 * q + l;
-            int64_t p = e < n ? e : e % n;
+            int64_t p = e < n ? e : (e < 2 * n ? e - n : e % n);   // no 64-bit remainder in practice
             if (mode == MODE_I32_FAST) {
                 int32_t xi = x[p] - cx, yi = y[p] - cy, zi = z[p] - cz;
                 rec.x[l] = static_cast<float>(xi);
@@ -310,7 +342,7 @@ __global__ void k_fill_f32(const float *__restrict__ x, const float *__restrict_
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
             int64_t e = 2 * q + l;
-            int64_t p = e < n ? e : e % n;
+            int64_t p = e < n ? e : (e < 2 * n ? e - n : e % n);   // no 64-bit remainder in practice
             rec.x[l] = x[p];
             rec.y[l] = y[p];
             rec.z[l] = z[p];
@@ -1123,7 +1155,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
     const int64_t prep_blocks_full = (g.nrec + prep_threads - 1) / prep_threads;
     const int prep_blocks = static_cast<int>(std::min<int64_t>(prep_blocks_full, sm_count() * 8));
     if (!f32) {
-        const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+        const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 2));
         k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                  static_cast<const int32_t *>(p->y),
                                                  static_cast<const int32_t *>(p->z), n, r2, hdr,
@@ -1139,7 +1171,7 @@ cc_status single_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned lo
         }
     } else {
         if (tc) {
-            const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+            const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 2));
             k_minmax_f32<<<mm_blocks, 256, 0, stream>>>(static_cast<const float *>(p->x),
                                                          static_cast<const float *>(p->y),
                                                          static_cast<const float *>(p->z), p->r, n, hdr, 1);
@@ -1207,7 +1239,7 @@ cc_status straight_enqueue(const cc_points *p, int64_t n, uint32_t r2, unsigned 
     const int64_t nrec = ((n + JS - 1) / JS + 1) * JS / 2;   // see straight_ws_bytes
     const int blocks = static_cast<int>(std::min<int64_t>((nrec + 255) / 256, sm_count() * 8));
     if (!f32) {
-        const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+        const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 2));
         k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                                  static_cast<const int32_t *>(p->y),
                                                  static_cast<const int32_t *>(p->z), n, r2, hdr, d_count, 0,
@@ -1255,7 +1287,7 @@ cc_status validate_enqueue(const cc_points *p, int64_t n, void *ws, cudaStream_t
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     k_reset<<<1, 32, 0, stream>>>(hdr, MODE_I32_FAST, nullptr, nullptr);
     CC_CUDA(cudaGetLastError());
-    const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 4));
+    const int mm_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, sm_count() * 2));
     k_minmax<<<mm_blocks, 256, 0, stream>>>(static_cast<const int32_t *>(p->x),
                                              static_cast<const int32_t *>(p->y),
                                              static_cast<const int32_t *>(p->z), n, 0u, hdr, nullptr, 0, nullptr);

@@ -107,11 +107,12 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
     if (h->mode != (F32 ? MODE_F32_TC : MODE_I32_TC)) return;   // uniform over the grid
     const int32_t cx = h->cx, cy = h->cy, cz = h->cz;
     // integer points: 16 cells per axis over the bounding box, for the occupancy histogram
-    int64_t box_lo[3] = {0, 0, 0}, box_n[3] = {1, 1, 1};   // minimum and span + 1 per axis
+    // (in this mode every span is at most 2046, so the cell arithmetic fits 32 bits)
+    int32_t box_lo[3] = {0, 0, 0}, box_n[3] = {1, 1, 1};   // minimum and span + 1 per axis
     if (!F32 && hist) {
         for (int a = 0; a < 3; ++a) {
             box_lo[a] = ord_dec(h->umin[a]);
-            box_n[a] = static_cast<int64_t>(ord_dec(h->umax[a])) - box_lo[a] + 1;
+            box_n[a] = ord_dec(h->umax[a]) - box_lo[a] + 1;
         }
     }
     const int32_t off = h->ai_off;   // r2e + 1
@@ -126,9 +127,9 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
                 const int32_t xi = tc_coord<F32>(x, r, 0, h) - cx, yi = tc_coord<F32>(y, r, 1, h) - cy,
                               zi = tc_coord<F32>(z, r, 2, h) - cz;
                 if (!F32 && hist && (r & (TC_HIST_STRIDE - 1)) == 0) {   // every 8th object
-                    const int64_t qx = (static_cast<int64_t>(xi) + cx - box_lo[0]) * 16 / box_n[0];
-                    const int64_t qy = (static_cast<int64_t>(yi) + cy - box_lo[1]) * 16 / box_n[1];
-                    const int64_t qz = (static_cast<int64_t>(zi) + cz - box_lo[2]) * 16 / box_n[2];
+                    const int32_t qx = (xi + cx - box_lo[0]) * 16 / box_n[0];
+                    const int32_t qy = (yi + cy - box_lo[1]) * 16 / box_n[1];
+                    const int32_t qz = (zi + cz - box_lo[2]) * 16 / box_n[2];
                     atomicAdd(&hist[(qx * 16 + qy) * 16 + qz], 1u);
                 }
                 const int32_t c = xi * xi + yi * yi + zi * zi - off;
@@ -149,7 +150,9 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
             *reinterpret_cast<float4 *>(ga + tc_off(r, 4)) = hi;
         }
         if (r < elen) {
-            const int64_t p = r < n ? r : r % n;
+            // extended rows stay below 2n (elen < 2n for the sizes this path serves): a
+            // subtraction, not a 64-bit remainder, maps them back
+            const int64_t p = r < n ? r : (r < 2 * n ? r - n : r % n);
             const int32_t xj = tc_coord<F32>(x, p, 0, h) - cx, yj = tc_coord<F32>(y, p, 1, h) - cy,
                           zj = tc_coord<F32>(z, p, 2, h) - cz;
             const int32_t nj = xj * xj + yj * yj + zj * zj;
