@@ -80,9 +80,8 @@ struct WsHeader {
                           // 1 = walk the (rare) blocks with a hit (sparse hits expected)
     uint32_t cstatus;     // ST_* bits of the current call only (cleared by each call's
                           // reset); a non-zero value invalidates the call's outputs
-    uint32_t sbox[7];     // small-set kernel: per-axis ~min and max codes of the set, and a
-                          // flag for units that took the wide form (0 between calls)
     uint32_t sticket;     // small-set kernel: last-CTA ticket (0 between calls)
+    uint32_t pad[7];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 static_assert(int{MODE_I32_FAST} == int{CC_MODE_FP32_EXACT} && int{MODE_I32_WIDE} == int{CC_MODE_INT_WIDE} &&
