@@ -243,6 +243,11 @@ TC_FLOPS_PER_PAIR = 16
 # tcgen05.mma kind::tf32 M=128 N=256 K=8 (32768 pair tests each).
 TMEM_READ_BYTES_PER_CLK = 870
 MMA_CLK_PER_UNIT = 128.2
+# The kernel's accumulator hand-over loop with nothing else in it (one issuing thread, two
+# 256-column accumulators, eight epilogue warps loading and voting): SM clocks per unit,
+# measured by the same tool. Within the kernel's design this is the bound: a shared-memory
+# read that the next MMA issue waits for costs the issuing thread about 170-200 clocks.
+HANDOVER_CLK_PER_UNIT = 458.0
 PAIRS_PER_UNIT = 128 * 256
 # TF32 / BF16 dense tensor throughput ratio of the part's nominal figures (1.1 / 2.25 PF).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -384,8 +389,8 @@ def main():
         }
         # The kernel's own hardware bounds: every pair test's accumulator is read back from
         # TMEM (4 B per pair), and one MMA evaluates 32768 pair tests. Both measured on this
-        # GPU with the kernel's instruction shapes; the kernel runs well below either (its
-        # period is set by the latency of the accumulator hand-over chain).
+        # GPU with the kernel's instruction shapes; the kernel runs well below either. Its
+        # period is set by the accumulator hand-over loop, measured alone as a third bound.
         tmem_peak = sms * TMEM_READ_BYTES_PER_CLK * fmax * 1e6 / 4.0 / 1e9   # G pair tests/s
         roofline["tmem_read_bound"] = {
             "peak_pair_tests_per_s": tmem_peak,
@@ -400,6 +405,14 @@ def main():
             "frac": (pair_rate / mma_peak) if pair_rate else None,
             "basis": (f"one tcgen05.mma kind::tf32 128x256x8 (32768 pair tests) every {MMA_CLK_PER_UNIT} SM "
                       f"clocks (measured back to back) x {sms} SMs x {fmax:.0f} MHz"),
+        }
+        hand_peak = sms * PAIRS_PER_UNIT / HANDOVER_CLK_PER_UNIT * fmax * 1e6 / 1e9
+        roofline["handover_bound"] = {
+            "peak_pair_tests_per_s": hand_peak,
+            "frac": (pair_rate / hand_peak) if pair_rate else None,
+            "basis": (f"the kernel's accumulator hand-over loop alone (one MMA-issuing thread, two 256-column "
+                      f"accumulators, eight epilogue warps loading and voting): {HANDOVER_CLK_PER_UNIT} SM clocks "
+                      f"per 32768 pair tests (measured) x {sms} SMs x {fmax:.0f} MHz"),
         }
     else:
         traffic, traffic_note = measured_traffic("fp32")
