@@ -151,8 +151,9 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
     int64_t m = 0, dmax = 0;
     bool range_ok = true;
     for (int a = 0; a < 3; ++a) {
-        lo[a] = ord_dec(atomicAdd(&h->umin[a], 0u));
-        int64_t hi = ord_dec(atomicAdd(&h->umax[a], 0u));
+        // L2 reads (the per-block atomics above are all in L2 and fenced by the ticket)
+        lo[a] = ord_dec(__ldcg(&h->umin[a]));
+        int64_t hi = ord_dec(__ldcg(&h->umax[a]));
         span[a] = hi - lo[a];
         if (span[a] > WIDE_MAX_SPAN) range_ok = false;
         m = max(m, (span[a] + 1) / 2);
@@ -178,13 +179,14 @@ __global__ void k_minmax(const int32_t *__restrict__ x, const int32_t *__restric
     // bounding box, (lattice points within the r2 ball) / (box sites), bounded above by
     // the ball of radius sqrt(r2) + 1. Below TC_SPARSE_HITS the walk form (a lean loop;
     // measured +9 % at 1e-7) runs, above it the in-register count (+19 % at 3e-5).
-    // Either form gives the exact count; only the speed depends on the choice.
+    // Either form gives the exact count; only the speed depends on the choice, so the
+    // estimate is FP32 (a dependent FP64 chain is slow on this part's FP64 pipe).
     {
-        const double rad = sqrt(static_cast<double>(r2e)) + 1.0;
-        const double ball = 4.18879020478639 * rad * rad * rad;   // (4/3) pi rad^3
-        const double sites = static_cast<double>(span[0] + 1) * static_cast<double>(span[1] + 1) *
-                             static_cast<double>(span[2] + 1);
-        h->tc_form = ball < TC_SPARSE_HITS * sites ? 1 : 0;
+        const float rad = sqrtf(static_cast<float>(r2e)) + 1.0f;
+        const float ball = 4.18879020f * rad * rad * rad;   // (4/3) pi rad^3
+        const float sites = static_cast<float>(span[0] + 1) * static_cast<float>(span[1] + 1) *
+                            static_cast<float>(span[2] + 1);
+        h->tc_form = ball < static_cast<float>(TC_SPARSE_HITS) * sites ? 1 : 0;
     }
     h->r2e = static_cast<uint32_t>(r2e);
     h->ai_off = static_cast<int32_t>(r2e + 1);

@@ -168,9 +168,11 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
     // one object in TC_HIST_STRIDE): pairs that share a cell,
     // times the chance that a pair inside one cell is within reach (ball / cell sites),
     // and never below the bounding-box estimate. Clustered sets, whose bounding box hides
-    // their density, then take the in-register form.
+    // their density, then take the in-register form. The pair counts are exact integers
+    // and the estimate FP32: it only picks the faster of two exact forms, and the FP64
+    // pipe of this part is slow enough that the same tail in FP64 took about 13 us.
     __shared__ bool last;
-    __shared__ double red[32];
+    __shared__ unsigned long long red[32];
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -179,26 +181,25 @@ __global__ void k_fill_tc(const void *__restrict__ x, const void *__restrict__ y
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double same = 0.0;
+    unsigned long long same = 0;
     for (int c = threadIdx.x; c < TC_HIST_CELLS; c += blockDim.x) {
-        const double k = static_cast<double>(__ldcg(&hist[c]));
-        same += 0.5 * k * (k - 1.0);
+        const unsigned long long k = __ldcg(&hist[c]);
+        same += k * (k - 1) / 2;   // 0 when k = 0 (the wrapped factor is multiplied by 0)
     }
     for (int o = 16; o > 0; o >>= 1) same += __shfl_down_sync(0xFFFFFFFFu, same, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = same;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tot = 0.0;
+        unsigned long long tot = 0;
         for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += red[w];
-        const double ns = static_cast<double>((n + TC_HIST_STRIDE - 1) / TC_HIST_STRIDE);   // sampled
-        const double pairs = 0.5 * ns * (ns - 1.0);
-        const double rad = sqrt(static_cast<double>(h->r2e)) + 1.0;
-        const double ball = 4.18879020478639 * rad * rad * rad;   // (4/3) pi rad^3
-        const double sites = static_cast<double>(box_n[0]) * static_cast<double>(box_n[1]) *
-                             static_cast<double>(box_n[2]);
-        const double cell_sites = sites / TC_HIST_CELLS;
-        const double est = fmax(ball / sites, (tot / pairs) * fmin(1.0, ball / cell_sites));
-        h->tc_form = est < TC_SPARSE_HITS ? 1 : 0;
+        const float ns = static_cast<float>((n + TC_HIST_STRIDE - 1) / TC_HIST_STRIDE);   // sampled
+        const float pairs = 0.5f * ns * (ns - 1.0f);
+        const float rad = sqrtf(static_cast<float>(h->r2e)) + 1.0f;
+        const float ball = 4.18879020f * rad * rad * rad;   // (4/3) pi rad^3
+        const float sites = static_cast<float>(box_n[0]) * static_cast<float>(box_n[1]) * static_cast<float>(box_n[2]);
+        const float cell_sites = sites / static_cast<float>(TC_HIST_CELLS);
+        const float est = fmaxf(ball / sites, (static_cast<float>(tot) / pairs) * fminf(1.0f, ball / cell_sites));
+        h->tc_form = est < static_cast<float>(TC_SPARSE_HITS) ? 1 : 0;
         h->ticket0 = 0;
     }
 }
