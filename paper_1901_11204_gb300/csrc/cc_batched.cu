@@ -103,12 +103,24 @@ __device__ __forceinline__ const Band &band_of(const BandTable &bt, int64_t n) {
     return bt.band[bt.count - 1];
 }
 
-__host__ __device__ __forceinline__ int64_t tile_of(const Band &b) { return 32 * static_cast<int64_t>(b.r); }
+// The helpers below take the integer type I: int64_t on the host (a plan's point budget
+// may pass 2^31), int32_t on the device, where every set has fewer than 2^31 objects
+// (larger sets are flagged by the prepare kernel) and a 32-bit division by the band's
+// runtime widths costs a fraction of a 64-bit one (these run once per set and per item).
+template <typename I>
+__host__ __device__ __forceinline__ I tile_of(const Band &b) { return 32 * static_cast<I>(b.r); }
+
+// Tiles of a set, ceil(n / T), written so that n close to the largest I cannot overflow.
+template <typename I>
+__host__ __device__ __forceinline__ I tiles_of(const Band &b, I n) {
+    return n > 0 ? (n - 1) / tile_of<I>(b) + 1 : 0;
+}
 
 // Stages (of kJSB objects) in one tile's extended j-range: offsets 0 .. T + h.
-__host__ __device__ __forceinline__ int64_t stages_of(const Band &b, int64_t n) {
-    const int64_t h = (n - 1) / 2;
-    return (tile_of(b) + h + 1 + kJSB - 1) / kJSB;
+template <typename I>
+__host__ __device__ __forceinline__ I stages_of(const Band &b, I n) {
+    const I h = (n - 1) / 2;
+    return (tile_of<I>(b) + h + 1 + kJSB - 1) / kJSB;
 }
 
 // Most work items one set may produce, beyond one per tile: without a bound the items of a
@@ -117,27 +129,31 @@ constexpr int64_t kMaxItemsPerSet = 16384;
 
 // Stages (of kJSB objects) per work item: the band's sc (0 = the whole tile range),
 // widened where needed so that a set has at most max(tiles, kMaxItemsPerSet) items.
-__host__ __device__ __forceinline__ int64_t chunk_stages(const Band &b, int64_t n) {
-    const int64_t K = stages_of(b, n);
-    const int64_t T = tile_of(b);
-    const int64_t M = (n + T - 1) / T;
-    int64_t per = b.sc > 0 ? b.sc : K;
-    const int64_t maxch = kMaxItemsPerSet / M > 1 ? kMaxItemsPerSet / M : 1;
+template <typename I>
+__host__ __device__ __forceinline__ I chunk_stages(const Band &b, I n) {
+    const I K = stages_of<I>(b, n);
+    const I M = tiles_of<I>(b, n);
+    I per = b.sc > 0 ? static_cast<I>(b.sc) : K;
+    const I cap = static_cast<I>(kMaxItemsPerSet);
+    const I maxch = cap / M > 1 ? cap / M : 1;
     if ((K + per - 1) / per > maxch) per = (K + maxch - 1) / maxch;
     return per;
 }
 
-__host__ __device__ __forceinline__ int64_t chunks_of(const Band &b, int64_t n) {
-    const int64_t K = stages_of(b, n);
-    const int64_t per = chunk_stages(b, n);
+template <typename I>
+__host__ __device__ __forceinline__ I chunks_of(const Band &b, I n) {
+    const I K = stages_of<I>(b, n);
+    const I per = chunk_stages<I>(b, n);
     return (K + per - 1) / per;
 }
 
-__host__ __device__ __forceinline__ int64_t items_of(const Band &b, int64_t n) {
+// Work items of a set: tiles times chunks, at most max(tiles, kMaxItemsPerSet) (so it
+// fits I whenever n does).
+template <typename I>
+__host__ __device__ __forceinline__ I items_of(const Band &b, I n) {
     if (n < 2) return 0;
     if (b.r == 0) return 1;   // warp-per-set shuffle path (sets of at most 32 objects)
-    const int64_t T = tile_of(b);
-    return ((n + T - 1) / T) * chunks_of(b, n);
+    return tiles_of<I>(b, n) * chunks_of<I>(b, n);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -182,6 +198,10 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, Se
             if (lane == 0) sets[k] = d;
         } else {
             d = sets[k];
+            if (d.n < 0 || d.n >= (int64_t(1) << 31)) {   // the per-set arithmetic is 32-bit
+                flag = SET_BAD_OFFSETS;
+                d.n = 0;
+            }
         }
         SetAux x{};
         x.mode = MODE_F32;
@@ -251,7 +271,8 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, Se
         }
         if (lane == 0) {
             aux[k] = x;
-            const int64_t it = flag == SET_OK ? items_of(band_of(*bt, d.n), d.n) : 0;
+            const int64_t it =
+                flag == SET_OK ? items_of<int32_t>(band_of(*bt, d.n), static_cast<int32_t>(d.n)) : 0;
             cnt[k] = static_cast<int32_t>(it < 0x7FFFFFFF ? it : 0x7FFFFFFF);
             flags[k] = flag;
         }
@@ -335,11 +356,11 @@ __device__ void run_item(const SetDesc &d, const SetAux &x, const Band &b, int32
     constexpr int T = 32 * R;
     const int32_t n = static_cast<int32_t>(d.n);
     const int32_t h = (n - 1) / 2;
-    const int32_t M = (n + T - 1) / T;
-    const int32_t K = static_cast<int32_t>(stages_of(b, n));
+    const int32_t M = (n - 1) / T + 1;   // n >= 2 here; T is a constant
+    const int32_t K = stages_of<int32_t>(b, n);
     const int32_t tile = local % M;
     const int32_t chunk = local / M;
-    const int32_t per = static_cast<int32_t>(chunk_stages(b, n));
+    const int32_t per = chunk_stages<int32_t>(b, n);
     const int32_t k0 = chunk * per;
     const int32_t k1 = min(k0 + per, K);
     const int32_t tile0 = tile * T;
@@ -607,8 +628,8 @@ static double items_per_object(const BandTable &t, int64_t max_n) {
         const int64_t hi = std::min(t.band[b].n_max, max_n);
         // sample the band densely near its ends and geometrically inside
         for (int64_t n = lo; n <= hi; n = (n < lo + 4096 ? n + 1 : n + n / 64 + 1))
-            worst = std::max(worst, static_cast<double>(items_of(t.band[b], n)) / n);
-        worst = std::max(worst, static_cast<double>(items_of(t.band[b], hi)) / hi);
+            worst = std::max(worst, static_cast<double>(items_of<int64_t>(t.band[b], n)) / n);
+        worst = std::max(worst, static_cast<double>(items_of<int64_t>(t.band[b], hi)) / hi);
         lo = hi + 1;
     }
     return worst;
