@@ -8,7 +8,8 @@ metric: G pair-tests/s = sum of N(N-1)/2 over the step / device time of the step
 
 Also measured in the same run (secondary keys of the JSON line):
   e2e          the same step through the C ABI with host inputs: pinned host->device
-               copies and the device->host read of the counts inside the timed region;
+               copies and the device->host read of the counts inside the timed region
+               (the copies of the next set overlap the count of the current one);
   roofline     dominant kernel (the pair kernel), timed with CUDA events on its stream;
   cpu_baseline the CPU oracle (plain pairwise loop) on the host cores, full step once;
   f32_spheres  N = 131072 FP32 spheres: count and interaction sum;
@@ -446,24 +447,40 @@ def main():
     h2d = sum(sum(t.numel() * t.element_size() for t in hs) for hs in hsets)
     d2h = hout.numel() * hout.element_size()
 
-    def e2e_step():
+    # The copies of set k + 1 run on a copy stream while set k is counted: the copy stream
+    # starts each step after the step's start event (every copy is inside the timed
+    # region) and refills a set's buffers only after the previous count of that set.
+    copy_stream = torch.cuda.Stream(device=dev)
+    landed = [torch.cuda.Event() for _ in sets]
+    counted = [torch.cuda.Event() for _ in sets]
+
+    def e2e_step(start):
+        copy_stream.wait_event(start)
         for k, ((hx, hy, hz), (x, y, z, r2)) in enumerate(zip(hsets, dsets)):
-            x.copy_(hx, non_blocking=True)
-            y.copy_(hy, non_blocking=True)
-            z.copy_(hz, non_blocking=True)
+            copy_stream.wait_event(counted[k])
+            with torch.cuda.stream(copy_stream):
+                x.copy_(hx, non_blocking=True)
+                y.copy_(hy, non_blocking=True)
+                z.copy_(hz, non_blocking=True)
+            landed[k].record(copy_stream)
+        for k, (x, y, z, r2) in enumerate(dsets):
+            stream.wait_event(landed[k])
             cc.count_pairs(x, y, z, r2=r2, out=outs[k])
+            counted[k].record(stream)
         for k in range(len(outs)):
             hout[k:k + 1].copy_(outs[k], non_blocking=True)
 
     for _ in range(2):
-        e2e_step()
+        w = torch.cuda.Event()
+        w.record(stream)
+        e2e_step(w)
     torch.cuda.synchronize()
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     for k in range(args.steps):
         flush.fill_(k)
         ee[k][0].record(stream)
-        e2e_step()
+        e2e_step(ee[k][0])
         ee[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
