@@ -9,7 +9,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 
 
-def main() -> int:
+def build() -> str:
+    """Compiles the microbenchmark for sm_103a (the package's nvcc and architecture flags)
+    and returns the executable's path."""
     sys.path.insert(0, os.path.dirname(HERE))
     import builder  # noqa: E402  (the package's nvcc location and flags)
     out = os.path.join(HERE, "_build")
@@ -18,7 +20,11 @@ def main() -> int:
     cmd = [builder._nvcc(), *builder.ARCH, "-O3", "-std=c++17", "--expt-relaxed-constexpr",
            "-I" + os.path.join(ROOT, "include"), os.path.join(HERE, "tmem_mma_rates.cu"), "-o", exe]
     subprocess.run(cmd, check=True)
-    return subprocess.run([exe]).returncode
+    return exe
+
+
+def main() -> int:
+    return subprocess.run([build()]).returncode
 
 
 if __name__ == "__main__":
