@@ -83,3 +83,11 @@ def test_no_cpu_fallback_in_product_package():
                 src = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "cc_oracle" not in src, f
+
+
+def test_bounds_microbenchmark_compiles():
+    """The tool that measures the tensor-core kernel's bounds (TMEM reads, MMA issue, the
+    accumulator hand-over loop) cross-compiles for sm_103a from the committed sources."""
+    from paper_1901_11204_gb300.microbench import __main__ as microbench
+    exe = microbench.build()
+    assert os.path.isfile(exe) and os.path.getsize(exe) > 0
