@@ -249,12 +249,13 @@ struct TcSmem {
     static constexpr int kA = 0;                          // 2 i-tile slots
     static constexpr int kB = 2 * TC_ATILE;               // TC_NS j-stage slots
     static constexpr int kBars = kB + TC_NS * kStage;
-    // a_full[2] a_empty[2] ready[NS] b_empty[NS] t_full[NB] done
+    // a_full[2] a_empty[2] ready[NS] b_empty[NS] t_full[NB] done (t_full2[NB] at kFull2)
     static constexpr int kNBars = 5 + 2 * TC_NS + TC_NB;
     static constexpr int kMisc = kBars + kNBars * 8;      // tmem address, abort flag, copy drain words
     static constexpr int kRed = kMisc + 16;               // per-epilogue-warp counts
     static constexpr int kRedSum = kRed + TC_EPW * 8;     // per-epilogue-warp sums
-    static constexpr int kTotal = kRedSum + TC_EPW * 8;
+    static constexpr int kFull2 = kRedSum + TC_EPW * 8;   // t_full2[NB]
+    static constexpr int kTotal = kFull2 + TC_NB * 8;
 };
 
 __device__ __forceinline__ f2 f2_fma_rm(f2 a, f2 b, f2 c) {
@@ -342,6 +343,12 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 //                      unit and paced the pipeline. The slots of the share's last NB units
 //                      are never needed again and are not returned;
 //   t_full[NB]         accumulator written: tcgen05.commit after the unit's MMA;
+//   t_full2[NB]        the same, committed a second time in the in-register count form,
+//                      for warps 6-9 (the second epilogue warp of each SMSP): two warps
+//                      of an SMSP sleeping on one barrier woke one after the other, and
+//                      with a barrier each the form runs 3.6 % faster at dense hits; the
+//                      other forms keep one barrier (the second commit lengthens the MMA
+//                      thread's loop, their critical path: 8 % slower);
 //   done               every MMA of this CTA completed (before TMEM is freed).
 template <bool SUMT, bool SPH, bool WALKC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
@@ -360,6 +367,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
     uint64_t *a_full = bars, *a_empty = bars + 2;
     uint64_t *ready = bars + 4, *b_empty = bars + 4 + NS;
     uint64_t *t_full = bars + 4 + 2 * NS, *done = t_full + NB;
+    // in-register count form: the second epilogue warp of each SMSP waits here (after the
+    // other buffers, so that the other forms' layout and code stay as they were)
+    uint64_t *t_full2 = reinterpret_cast<uint64_t *>(smem + L::kFull2);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kMisc + 4);
     // the copy warp's number of issued stage copies, published when it stops (drain)
@@ -374,7 +384,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
-        for (int i = 0; i < NB; ++i) mbar_init(&t_full[i], 1);
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&t_full[i], 1);
+            if constexpr (!WALK) mbar_init(&t_full2[i], 1);
+        }
         for (int i = 0; i < NS; ++i) {
             mbar_init(&ready[i], 1 + EPW);
             mbar_init(&b_empty[i], 1);
@@ -487,6 +500,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
                 tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad0 + as * (TC_ATILE >> 4),
                             bd0 + static_cast<uint32_t>(slot) * (kStage >> 4), idesc, 0u);
                 tc_commit(&t_full[buf]);
+                if constexpr (!WALK) tc_commit(&t_full2[buf]);
                 new_tile = ++st == K32;
                 if (new_tile) st = 0;
                 if (++slot == NS) {
@@ -557,7 +571,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
         for (; q < nu; ++q) {
             const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
-            const bool got = __all_sync(0xFFFFFFFFu, mbar_sleep_bounded(&t_full[buf], fph, A.wait_ns, abort_flag));
+            const bool got = __all_sync(0xFFFFFFFFu, mbar_sleep_bounded(!WALK && ew >= 4 ? &t_full2[buf] : &t_full[buf], fph,
+                                                                        A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
                     flag_status(A.hdr, ST_TIMEOUT);
