@@ -346,12 +346,14 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 //                      unit and paced the pipeline. The slots of the share's last NB units
 //                      are never needed again and are not returned;
 //   t_full[NB]         accumulator written: tcgen05.commit after the unit's MMA;
-//   t_full2[NB]        the same, committed a second time in the in-register count form,
-//                      for warps 6-9 (the second epilogue warp of each SMSP): two warps
-//                      of an SMSP sleeping on one barrier woke one after the other, and
-//                      with a barrier each the form runs 3.6 % faster at dense hits; the
-//                      other forms keep one barrier (the second commit lengthens the MMA
-//                      thread's loop, their critical path: 8 % slower);
+//   t_full2[NB]        the same, committed a second time in the in-register count form
+//                      and the FP32-sphere sum (FULL2), for warps 6-9 (the second
+//                      epilogue warp of each SMSP): two warps of an SMSP sleeping on one
+//                      barrier woke one after the other, and with a barrier each those
+//                      forms run 3.6 % faster (in-register count at dense hits, sphere
+//                      sums); the others keep one barrier, where the second commit
+//                      lengthens the MMA thread's loop, their critical path (walk count
+//                      8 %, integer sum at sparse hits 6 %, sphere count 4.5 % slower);
 //   done               every MMA of this CTA completed (before TMEM is freed).
 template <bool SUMT, bool SPH, bool WALKC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
@@ -359,6 +361,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
     constexpr int JS = TC_JS, NB = TC_NB, EPW = TC_EPW, NS = TC_NS, CPW = TC_CPW;
     constexpr int kStage = L::kStage;
     constexpr bool WALK = SUMT || SPH || WALKC;   // screened values are walked one by one
+    // forms whose second epilogue warp of each SMSP waits on its own accumulator barrier
+    constexpr bool FULL2 = !WALK || (SUMT && SPH);
     extern __shared__ __align__(1024) uint8_t smem[];
     // uniform: another kernel handles this call
     if (A.hdr->mode != (SPH ? MODE_F32_TC : MODE_I32_TC)) return;
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
     uint64_t *a_full = bars, *a_empty = bars + 2;
     uint64_t *ready = bars + 4, *b_empty = bars + 4 + NS;
     uint64_t *t_full = bars + 4 + 2 * NS, *done = t_full + NB;
-    // in-register count form: the second epilogue warp of each SMSP waits here (after the
+    // FULL2 forms: the second epilogue warp of each SMSP waits here (after the
     // other buffers, so that the other forms' layout and code stay as they were)
     uint64_t *t_full2 = reinterpret_cast<uint64_t *>(smem + L::kFull2);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kMisc);
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
         }
         for (int i = 0; i < NB; ++i) {
             mbar_init(&t_full[i], 1);
-            if constexpr (!WALK) mbar_init(&t_full2[i], 1);
+            if constexpr (FULL2) mbar_init(&t_full2[i], 1);
         }
         for (int i = 0; i < NS; ++i) {
             mbar_init(&ready[i], 1 + EPW);
@@ -503,7 +507,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
                 tc_mma_tf32(tbase + static_cast<uint32_t>(buf * JS), ad0 + as * (TC_ATILE >> 4),
                             bd0 + static_cast<uint32_t>(slot) * (kStage >> 4), idesc, 0u);
                 tc_commit(&t_full[buf]);
-                if constexpr (!WALK) tc_commit(&t_full2[buf]);
+                if constexpr (FULL2) tc_commit(&t_full2[buf]);
                 new_tile = ++st == K32;
                 if (new_tile) st = 0;
                 if (++slot == NS) {
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(TcArgs A) {
         for (; q < nu; ++q) {
             const int32_t eo0 = st * JS;
             // warp-uniform outcome: the TMEM loads below are .sync.aligned
-            const bool got = __all_sync(0xFFFFFFFFu, mbar_sleep_bounded(!WALK && ew >= 4 ? &t_full2[buf] : &t_full[buf], fph,
+            const bool got = __all_sync(0xFFFFFFFFu, mbar_sleep_bounded(FULL2 && ew >= 4 ? &t_full2[buf] : &t_full[buf], fph,
                                                                         A.wait_ns, abort_flag));
             if (!got) {
                 if (lane == 0) {
