@@ -697,7 +697,8 @@ def bench_f32(cc, torch, dev, sms, fmax, peak_src, peaks):
 
 def bench_i32_sums(cc, torch, dev, n=262144):
     """Interaction sums of integer points on both kernels (tensor-core and FP32 pipe),
-    on the headline workload's first set at two hit densities."""
+    on the headline workload's first set at two hit densities, and the count at the dense
+    one (the tensor-core kernel's in-register count form)."""
     c = synth.cfg2(n)
     t = [torch.from_numpy(c[k]).to(dev) for k in ("x", "y", "z")]
     out = {"workload": f"N={n} int32 points uniform in [0,1024)^3"}
@@ -719,6 +720,21 @@ def bench_i32_sums(cc, torch, dev, n=262144):
         row["counts_equal"] = a["count"] == b["count"]
         row["sum_rel_diff"] = abs(a["sum"] - b["sum"]) / max(abs(b["sum"]), 1e-30)
         out[f"r2={r2}"] = row
+    # the count at the dense radius: the tensor-core kernel's in-register count form
+    row = {}
+    for tc in (True, False):
+        cc.set_tensor_cores(tc)
+        try:
+            ms = _time(lambda: cc.count_pairs(t[0], t[1], t[2], r2=400), 10, torch)
+            cnt = cc.count_pairs(t[0], t[1], t[2], r2=400)
+            torch.cuda.synchronize()
+            mode = cc.stream_mode()
+        finally:
+            cc.set_tensor_cores(True)
+        row["tensor" if tc else "fp32_pipe"] = {"count_ms": ms, "count_gpairs_s": pairs(n) / (ms * 1e-3) / 1e9,
+                                                "mode": mode, "count": cc.as_u64(cnt)}
+    row["counts_equal"] = row["tensor"]["count"] == row["fp32_pipe"]["count"]
+    out["count_r2=400"] = row
     return out
 
 
