@@ -2,8 +2,9 @@
 
 For every size band it times cc_count_pairs_batched on a synthetic batch of sets whose
 sizes fall in that band, for each candidate (R objects per lane, i.e. warp tiles of 32*R
-objects; SC stages of 64 objects per work item, 0 = the whole tile range), and keeps the
-fastest. The result is a JSON table that cc_plan_create accepts:
+objects; SC stages of 64 objects per work item, 0 = the whole tile range; for bands of at
+most 256 objects also R = 0, one warp per set with the whole set in shared memory), and
+keeps the fastest. The result is a JSON table that cc_plan_create accepts:
 
     {"gpu": "...", "sms": 152, "bands": [{"n_max": 64, "r": 1, "sc": 64}, ...],
      "timings_ms": {...}}
@@ -19,7 +20,8 @@ import statistics
 
 import numpy as np
 
-DEFAULT_BANDS = [(32, 0, 0), (64, 1, 8), (512, 2, 8), (8192, 4, 8), (-1, 4, 64)]
+DEFAULT_BANDS = [(32, 0, 0), (64, 0, 0), (128, 0, 0), (256, 0, 0), (512, 2, 8), (8192, 4, 8), (-1, 4, 64)]
+WARP_SET_MAX = 256   # largest set the one-warp-per-set path (R = 0) takes
 R_CHOICES = (1, 2, 4)
 SC_CHOICES = (0, 2, 4, 8, 16, 32, 64)
 
@@ -62,7 +64,13 @@ def tune(points_per_band: int = 400_000, reps: int = 5, r_choices=R_CHOICES, sc_
         t = [torch.from_numpy(a).to(dev) for a in (x, y, z, off)]
         best = None
         ref = None
-        cands = [(0, 0)] if r0 == 0 else [(r, sc) for r in r_choices for sc in sc_choices]
+        tiled = [(r, sc) for r in r_choices for sc in sc_choices]
+        if 0 < n_max <= 32:
+            cands = [(0, 0)]   # one object per lane, shuffles: always the fastest here
+        elif 0 < n_max <= WARP_SET_MAX:
+            cands = [(0, 0)] + tiled   # one warp per set, or tiles
+        else:
+            cands = tiled
         for r, sc in cands:
             if True:
                 cand = [list(b) for b in out_bands]

@@ -39,6 +39,7 @@ constexpr int kMaxBands = 8;
 constexpr int kScanBlock = 1024;
 constexpr int kJSB = 64;          // objects per staged j-stage
 constexpr int kMainWarps = 8;     // warps per CTA of the main kernel
+constexpr int kWarpSetMax = 256;  // largest set a band with r = 0 (one warp per set) may take
 
 struct Band {
     int64_t n_max;   // sets with n <= n_max (and above the previous band) use this band
@@ -152,7 +153,7 @@ __host__ __device__ __forceinline__ I chunks_of(const Band &b, I n) {
 template <typename I>
 __host__ __device__ __forceinline__ I items_of(const Band &b, I n) {
     if (n < 2) return 0;
-    if (b.r == 0) return 1;   // warp-per-set shuffle path (sets of at most 32 objects)
+    if (b.r == 0) return 1;   // one warp per set (sets of at most kWarpSetMax objects)
     return tiles_of<I>(b, n) * chunks_of<I>(b, n);
 }
 
@@ -396,6 +397,80 @@ __device__ __forceinline__ void run_item_mode(const SetDesc &d, const SetAux &x,
     else run_item<MODE_I32_WIDE, R, SUM>(d, x, b, local, slot, c, s);
 }
 
+// ---- one warp per set (band r = 0): sets of at most kWarpSetMax objects -----------------
+
+// One object in the convention of the warp-per-set paths: centred coordinates and |p'|^2
+// (integers below 2^24, exact in FP32) for the fast integer form, the caller's values and
+// radius for FP32 spheres, the int32 bits for the wide integer form.
+template <int MODE>
+__device__ __forceinline__ float4 set_obj(const SetDesc &d, const SetAux &x, int32_t i) {
+    if (MODE == MODE_I32_FAST) {
+        const int32_t a = static_cast<const int32_t *>(d.x)[i] - x.cx;
+        const int32_t b = static_cast<const int32_t *>(d.y)[i] - x.cy;
+        const int32_t c = static_cast<const int32_t *>(d.z)[i] - x.cz;
+        return make_float4(static_cast<float>(a), static_cast<float>(b), static_cast<float>(c),
+                           static_cast<float>(a * a + b * b + c * c));
+    } else if (MODE == MODE_F32) {
+        return make_float4(static_cast<const float *>(d.x)[i], static_cast<const float *>(d.y)[i],
+                           static_cast<const float *>(d.z)[i], d.r[i]);
+    } else {
+        return make_float4(__int_as_float(static_cast<const int32_t *>(d.x)[i]),
+                           __int_as_float(static_cast<const int32_t *>(d.y)[i]),
+                           __int_as_float(static_cast<const int32_t *>(d.z)[i]), 0.0f);
+    }
+}
+
+// An object tested against partners: its value and, for the fast form, the coefficients of
+// d^2 - r2 - 1 = n_j - 2 p'_i.p'_j + (n_i - r2 - 1).
+struct OwnObj {
+    float4 p;
+    float ax, ay, az, di;
+};
+
+template <int MODE>
+__device__ __forceinline__ OwnObj own_obj(float4 p, const SetAux &x) {
+    OwnObj o;
+    o.p = p;
+    o.ax = -2.0f * p.x;
+    o.ay = -2.0f * p.y;
+    o.az = -2.0f * p.z;
+    o.di = MODE == MODE_I32_FAST ? static_cast<float>(static_cast<int32_t>(p.w) - x.ai_off) : 0.0f;
+    return o;
+}
+
+// One pair test of an own object against partner q (the predicate of the mode, exact for
+// integers, in the specified FP32 rounding for spheres); with SUM the interaction term of
+// a hit is added to sum.
+template <int MODE, bool SUM>
+__device__ __forceinline__ uint32_t pair_test(const OwnObj &o, float4 q, const SetAux &x, double &sum) {
+    uint32_t hit;
+    uint32_t d2i = 0;
+    if (MODE == MODE_I32_FAST) {
+        const float v = __fadd_rn(__fmaf_rn(o.az, q.z, __fmaf_rn(o.ay, q.y, __fmaf_rn(o.ax, q.x, q.w))), o.di);
+        hit = __float_as_uint(v) >> 31;
+        if (SUM) {
+            const int32_t ex = static_cast<int32_t>(o.p.x) - static_cast<int32_t>(q.x);
+            const int32_t ey = static_cast<int32_t>(o.p.y) - static_cast<int32_t>(q.y);
+            const int32_t ez = static_cast<int32_t>(o.p.z) - static_cast<int32_t>(q.z);
+            d2i = static_cast<uint32_t>(ex * ex + ey * ey + ez * ez);
+        }
+    } else if (MODE == MODE_F32) {
+        hit = sphere_hit(o.p.x, o.p.y, o.p.z, o.p.w, q.x, q.y, q.z, q.w);
+    } else {
+        d2i = wide_d2(o.p.x, o.p.y, o.p.z, q.x, q.y, q.z);
+        hit = d2i <= x.r2e ? 1u : 0u;
+    }
+    if (SUM && hit) {
+        if (MODE == MODE_F32) {
+            const float dx = __fsub_rn(o.p.x, q.x), dy = __fsub_rn(o.p.y, q.y), dz = __fsub_rn(o.p.z, q.z);
+            sum += term_from_d2f(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+        } else {
+            sum += term_from_d2f(static_cast<float>(d2i));
+        }
+    }
+    return hit;
+}
+
 // Sets of at most 32 objects: lane l holds object l and, at step s, gets its partner
 // (l + s) mod n from another lane by shuffles: the proposed algorithm with one object per
 // lane, exactly evals(i) tests per object and no staging or masks.
@@ -406,72 +481,63 @@ __device__ void run_tiny(const SetDesc &d, const SetAux &x, unsigned long long &
     const int32_t h = (n - 1) / 2;
     const bool even = (n & 1) == 0;
     const bool valid = lane < n;
-    const int32_t i = valid ? lane : 0;
-    float xi, yi, zi, wi;   // own object, in the staged-record convention
-    if (MODE == MODE_I32_FAST) {
-        const int32_t a = static_cast<const int32_t *>(d.x)[i] - x.cx;
-        const int32_t b = static_cast<const int32_t *>(d.y)[i] - x.cy;
-        const int32_t c = static_cast<const int32_t *>(d.z)[i] - x.cz;
-        xi = static_cast<float>(a);
-        yi = static_cast<float>(b);
-        zi = static_cast<float>(c);
-        wi = static_cast<float>(a * a + b * b + c * c);
-    } else if (MODE == MODE_F32) {
-        xi = static_cast<const float *>(d.x)[i];
-        yi = static_cast<const float *>(d.y)[i];
-        zi = static_cast<const float *>(d.z)[i];
-        wi = d.r[i];
-    } else {
-        xi = __int_as_float(static_cast<const int32_t *>(d.x)[i]);
-        yi = __int_as_float(static_cast<const int32_t *>(d.y)[i]);
-        zi = __int_as_float(static_cast<const int32_t *>(d.z)[i]);
-        wi = 0.0f;
-    }
-    const float ax = -2.0f * xi, ay = -2.0f * yi, az = -2.0f * zi;
-    const float di = static_cast<float>(static_cast<int32_t>(wi) - x.ai_off);
+    const OwnObj o = own_obj<MODE>(set_obj<MODE>(d, x, valid ? lane : 0), x);
     const int32_t steps = h + (even ? 1 : 0);
     uint32_t cnt = 0;
     double sum = 0.0;
     int32_t src = lane + 1 < n ? lane + 1 : lane + 1 - n;
     for (int32_t s = 1; s <= steps; ++s) {
-        const float xj = __shfl_sync(0xFFFFFFFFu, xi, src);
-        const float yj = __shfl_sync(0xFFFFFFFFu, yi, src);
-        const float zj = __shfl_sync(0xFFFFFFFFu, zi, src);
-        const float wj = __shfl_sync(0xFFFFFFFFu, wi, src);
-        const bool ok = valid && (s <= h || lane < n / 2);
-        uint32_t hit;
-        uint32_t d2i = 0;
-        if (MODE == MODE_I32_FAST) {
-            const float v = __fadd_rn(__fmaf_rn(az, zj, __fmaf_rn(ay, yj, __fmaf_rn(ax, xj, wj))), di);
-            hit = __float_as_uint(v) >> 31;
-            if (SUM) {
-                const int32_t ex = static_cast<int32_t>(xi) - static_cast<int32_t>(xj);
-                const int32_t ey = static_cast<int32_t>(yi) - static_cast<int32_t>(yj);
-                const int32_t ez = static_cast<int32_t>(zi) - static_cast<int32_t>(zj);
-                d2i = static_cast<uint32_t>(ex * ex + ey * ey + ez * ez);
-            }
-        } else if (MODE == MODE_F32) {
-            hit = sphere_hit(xi, yi, zi, wi, xj, yj, zj, wj);
-        } else {
-            d2i = wide_d2(xi, yi, zi, xj, yj, zj);
-            hit = d2i <= x.r2e ? 1u : 0u;
-        }
-        hit = ok ? hit : 0u;
-        cnt += hit;
-        if (SUM && hit) {
-            if (MODE == MODE_F32) {
-                const float dx = __fsub_rn(xi, xj), dy = __fsub_rn(yi, yj), dz = __fsub_rn(zi, zj);
-                sum += term_from_d2f(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
-            } else {
-                sum += term_from_d2f(static_cast<float>(d2i));
-            }
-        }
+        float4 q;
+        q.x = __shfl_sync(0xFFFFFFFFu, o.p.x, src);
+        q.y = __shfl_sync(0xFFFFFFFFu, o.p.y, src);
+        q.z = __shfl_sync(0xFFFFFFFFu, o.p.z, src);
+        q.w = __shfl_sync(0xFFFFFFFFu, o.p.w, src);
+        // the even-N extra step (s = n/2) belongs to the objects i < n/2
+        if (valid && (s <= h || lane < n / 2)) cnt += pair_test<MODE, SUM>(o, q, x, sum);
         src = src + 1 < n ? src + 1 : 0;
     }
     unsigned long long c64 = cnt;
-    for (int o = 16; o > 0; o >>= 1) {
-        c64 += __shfl_down_sync(0xFFFFFFFFu, c64, o);
-        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        c64 += __shfl_down_sync(0xFFFFFFFFu, c64, o2);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o2);
+    }
+    cnt_out = c64;
+    sum_out = sum;
+}
+
+// Sets of 33 .. kWarpSetMax objects: the whole set in the warp's shared-memory buffer, lane
+// l owning objects l, l + 32, ..; at step s every owned object i tests (i + s) mod n read
+// from the buffer (consecutive lanes read consecutive objects). The proposed algorithm's
+// order with exactly evals(i) tests per object: no tiles, so no masked candidate pairs.
+template <int MODE, bool SUM>
+__device__ void run_warpset(const SetDesc &d, const SetAux &x, float4 *buf, unsigned long long &cnt_out,
+                            double &sum_out) {
+    const int lane = threadIdx.x & 31;
+    const int32_t n = static_cast<int32_t>(d.n);
+    const int32_t h = (n - 1) / 2;
+    const int32_t half = (n & 1) == 0 ? n / 2 : 0;   // objects below it take the extra step
+    __syncwarp();   // the previous item's reads of the buffer are done
+    for (int32_t i = lane; i < n; i += 32) buf[i] = set_obj<MODE>(d, x, i);
+    __syncwarp();
+    const int mo = (n + 31) >> 5;   // warp-uniform
+    uint32_t cnt = 0;
+    double sum = 0.0;
+    const int32_t steps = h + (half > 0 ? 1 : 0);
+    // one owned object at a time (few registers): its evals(i) partners in step order
+    for (int m = 0; m < mo; ++m) {
+        const int32_t i = lane + 32 * m;
+        const OwnObj o = own_obj<MODE>(buf[i < n ? i : 0], x);
+        const int32_t ev = i < n ? (i < half ? steps : h) : 0;
+        int32_t j = i + 1 < n ? i + 1 : i + 1 - n;
+        for (int32_t s = 1; s <= steps; ++s) {
+            if (s <= ev) cnt += pair_test<MODE, SUM>(o, buf[j], x, sum);
+            j = j + 1 < n ? j + 1 : 0;
+        }
+    }
+    unsigned long long c64 = cnt;
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        c64 += __shfl_down_sync(0xFFFFFFFFu, c64, o2);
+        if (SUM) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o2);
     }
     cnt_out = c64;
     sum_out = sum;
@@ -482,9 +548,16 @@ __device__ __forceinline__ void run_item_r(const SetDesc &d, const SetAux &x, co
                                            Rec *slot, unsigned long long &c, double &s) {
     switch (b.r) {
         case 0:
-            if (x.mode == MODE_I32_FAST) run_tiny<MODE_I32_FAST, SUM>(d, x, c, s);
-            else if (x.mode == MODE_F32) run_tiny<MODE_F32, SUM>(d, x, c, s);
-            else run_tiny<MODE_I32_WIDE, SUM>(d, x, c, s);
+            if (d.n <= 32) {
+                if (x.mode == MODE_I32_FAST) run_tiny<MODE_I32_FAST, SUM>(d, x, c, s);
+                else if (x.mode == MODE_F32) run_tiny<MODE_F32, SUM>(d, x, c, s);
+                else run_tiny<MODE_I32_WIDE, SUM>(d, x, c, s);
+            } else {   // the warp's buffer holds kWarpSetMax objects (the band table checks n_max)
+                float4 *buf = reinterpret_cast<float4 *>(slot);
+                if (x.mode == MODE_I32_FAST) run_warpset<MODE_I32_FAST, SUM>(d, x, buf, c, s);
+                else if (x.mode == MODE_F32) run_warpset<MODE_F32, SUM>(d, x, buf, c, s);
+                else run_warpset<MODE_I32_WIDE, SUM>(d, x, buf, c, s);
+            }
             break;
         case 1: run_item_mode<1, SUM>(d, x, b, local, slot, c, s); break;
         case 2: run_item_mode<2, SUM>(d, x, b, local, slot, c, s); break;
@@ -500,9 +573,11 @@ __global__ void __launch_bounds__(kMainWarps * 32, MINB) k_b_main(const BatchPar
                                                            const BandTable *bt, const Item *items,
                                                            BatchState *st, unsigned long long *pcnt,
                                                            double *psum) {
-    __shared__ Rec slots[kMainWarps][kJSB / 2];
+    // per warp: a j-stage of records (tiled items) or a whole set (one warp per set)
+    static_assert(kWarpSetMax * sizeof(float4) >= (kJSB / 2) * sizeof(Rec), "warp buffer");
+    __shared__ float4 wbuf[kMainWarps][kWarpSetMax];
     const int lane = threadIdx.x & 31;
-    Rec *slot = slots[threadIdx.x >> 5];
+    Rec *slot = reinterpret_cast<Rec *>(wbuf[threadIdx.x >> 5]);
     const int64_t total = st->total_items;
     const bool want_sum = P->want_sum != 0;
     unsigned long long *cursor = reinterpret_cast<unsigned long long *>(&st->cursor);
@@ -568,7 +643,7 @@ static BandTable default_bands() {
     BandTable t{};
     t.count = 5;
     t.band[0] = Band{32, 0, 0};
-    t.band[1] = Band{64, 1, 8};
+    t.band[1] = Band{kWarpSetMax, 0, 0};
     t.band[2] = Band{512, 2, 8};
     t.band[3] = Band{8192, 4, 8};
     t.band[4] = Band{INT64_MAX, 4, 64};
@@ -576,8 +651,8 @@ static BandTable default_bands() {
 }
 
 // Minimal parser for {"bands": [{"n_max": N, "r": R, "sc": S}, ...]} (n_max -1 = no limit;
-// r objects per lane in {1, 2, 4}, or 0 for the one-object-per-lane shuffle path of sets
-// of at most 32 objects; sc stages of 64 objects per work item, 0 = all).
+// r objects per lane in {1, 2, 4}, or 0 for one warp per set, sets of at most kWarpSetMax
+// objects (not the last band); sc stages of 64 objects per work item, 0 = all).
 static bool parse_bands(const char *json, BandTable &out, std::string &err) {
     BandTable t{};
     const char *p = strstr(json, "\"bands\"");
@@ -607,14 +682,15 @@ static bool parse_bands(const char *json, BandTable &out, std::string &err) {
             err = "r must be 0, 1, 2 or 4 and sc >= 0";
             return false;
         }
-        if (r == 0 && nmax > 32) {
-            err = "r = 0 (one object per lane) needs n_max <= 32";
+        if (r == 0 && (nmax < 0 || nmax > kWarpSetMax)) {
+            err = "r = 0 (one warp per set) needs 0 <= n_max <= " + std::to_string(kWarpSetMax);
             return false;
         }
         t.band[t.count++] = Band{nmax < 0 ? INT64_MAX : nmax, static_cast<int32_t>(r), static_cast<int32_t>(sc)};
         p = cb + 1;
     }
     if (t.count == 0) { err = "no bands"; return false; }
+    if (t.band[t.count - 1].r == 0) { err = "the last band (all larger sets) cannot have r = 0"; return false; }
     t.band[t.count - 1].n_max = INT64_MAX;
     out = t;
     return true;

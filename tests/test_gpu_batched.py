@@ -118,6 +118,9 @@ def test_custom_band_table_same_results(cc):
         {"bands": [{"n_max": -1, "r": 4, "sc": 3}]},
         {"bands": [{"n_max": -1, "r": 1, "sc": 0}]},
         {"bands": [{"n_max": 32, "r": 0, "sc": 0}, {"n_max": -1, "r": 2, "sc": 5}]},
+        {"bands": [{"n_max": 256, "r": 0, "sc": 0}, {"n_max": -1, "r": 4, "sc": 2}]},
+        {"bands": [{"n_max": 64, "r": 0, "sc": 0}, {"n_max": 128, "r": 1, "sc": 1},
+                   {"n_max": 200, "r": 0, "sc": 0}, {"n_max": -1, "r": 2, "sc": 0}]},
     ]
     for tb in tables:
         plan = cc.Plan(len(SIZES), len(x), json.dumps(tb) if tb else None)
@@ -150,3 +153,48 @@ def test_plan_memory_is_bounded(cc):
     used = free0 - torch.cuda.mem_get_info()[0]
     plan.close()
     assert used < (512 << 20), used
+
+
+WARP_SET_TABLE = {"bands": [{"n_max": 32, "r": 0, "sc": 0}, {"n_max": 256, "r": 0, "sc": 0},
+                            {"n_max": -1, "r": 2, "sc": 4}]}
+
+
+def test_warp_per_set_path_all_modes(cc):
+    """Sets of 33..256 objects on the one-warp-per-set path (band r = 0 up to 256): integer
+    sets in a narrow box (fast exact form) and a wide one (int difference form), counts and
+    interaction sums at several radii, and FP32 spheres with sums, against the oracle; sizes
+    around the warp multiples, odd and even, and on both sides of the path's limit."""
+    sizes = [33, 34, 47, 63, 64, 65, 95, 96, 97, 128, 129, 200, 255, 256, 257, 300, 2, 31, 32]
+    tb = json.dumps(WARP_SET_TABLE)
+    for box, radii in ((24, (0, 9, 400)), (5000, (250000, 4000000))):
+        x, y, z, _, off = make_sets(sizes, 11 + box, box=box)
+        t = to_dev(x, y, z, off)
+        plan = cc.Plan(len(sizes), len(x), tb)
+        for r2 in radii:
+            counts, sums = plan.count_pairs_batched(*t[:3], t[3], r2=r2, want_sum=True)
+            torch.cuda.synchronize()
+            want = oracle.count_i32_sets(x, y, z, off, r2)
+            assert np.array_equal(counts.cpu().numpy().view(np.uint64), want), (box, r2)
+            ws = np.array([oracle.sum_i32(x[a:b], y[a:b], z[a:b], r2)[1] for a, b in zip(off[:-1], off[1:])])
+            np.testing.assert_allclose(sums.cpu().numpy().astype(np.float64), ws, rtol=1e-5, atol=0)
+        plan.close()
+    x, y, z, r, off = make_sets(sizes, 17, f32=True)
+    t = to_dev(x, y, z, r, off)
+    plan = cc.Plan(len(sizes), len(x), tb)
+    counts, sums = plan.count_pairs_batched(*t[:3], t[4], r=t[3], want_sum=True)
+    torch.cuda.synchronize()
+    wc, ws = oracle.count_f32_sets(x, y, z, r, off)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint64), wc)
+    np.testing.assert_allclose(sums.cpu().numpy().astype(np.float64), ws, rtol=1e-5, atol=0)
+    plan.close()
+
+
+def test_band_table_rejects_bad_warp_set_bands(cc):
+    """A one-warp-per-set band (r = 0) above the path's 256 objects, or as the last band
+    (which takes every larger set), is refused when the plan is created."""
+    bad = [{"bands": [{"n_max": 257, "r": 0, "sc": 0}, {"n_max": -1, "r": 2, "sc": 4}]},
+           {"bands": [{"n_max": 32, "r": 0, "sc": 0}]},
+           {"bands": [{"n_max": 64, "r": 1, "sc": 1}, {"n_max": -1, "r": 0, "sc": 0}]}]
+    for tb in bad:
+        with pytest.raises(Exception):
+            cc.Plan(4, 100, json.dumps(tb))
