@@ -30,8 +30,10 @@ def _band_batch(lo: int, hi: int, total_points: int, seed: int):
     rng = np.random.default_rng(seed)
     sizes = []
     acc = 0
+    # sizes log-uniform within the band: set sizes are usually skewed (many small sets, few
+    # large ones), and a uniform draw would weigh the band's top end most
     while acc < total_points:
-        n = int(rng.integers(lo, hi + 1))
+        n = int(min(hi, max(lo, round(float(np.exp(rng.uniform(np.log(lo), np.log(hi + 1))))))))
         sizes.append(n)
         acc += n
     sizes = np.array(sizes, dtype=np.int64)
