@@ -185,9 +185,13 @@ cc_status cc_count_pairs_noalloc(const cc_points *p, int64_t n, uint32_t r2,
 
 typedef struct cc_plan cc_plan;
 
-/* Creates a batching plan: tile shapes per size band (from tune_table_json, a JSON
- * object as written by the autotuner, or built-in defaults when NULL) and device
- * work-queue storage. max_sets and max_points bound the batches it accepts. */
+/* Creates a batching plan: the work shape per size band (from tune_table_json, a JSON
+ * object as written by the autotuner, {"bands": [{"n_max": N, "r": R, "sc": S}, ...]},
+ * or built-in defaults when NULL: R objects per lane in warp tiles of 32*R objects and S
+ * stages of 64 objects per work item, or R = 0 for one warp per set, allowed for bands
+ * of at most 256 objects and not for the last band) and device work-queue storage.
+ * max_sets and max_points bound the batches it accepts. A table that breaks these rules
+ * gives CC_ERR_INVALID_ARG (cc_last_error() says why). */
 cc_status cc_plan_create(cc_plan **plan, const char *tune_table_json,
                          int32_t max_sets, int64_t max_points);
 void cc_plan_destroy(cc_plan *plan);
