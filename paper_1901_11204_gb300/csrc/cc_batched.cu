@@ -159,8 +159,15 @@ __host__ __device__ __forceinline__ I items_of(const Band &b, I n) {
 
 // ---------------------------------------------------------------------------------------
 
+template <int MODE, bool SUM>
+__device__ void run_tiny(const SetDesc &d, const SetAux &x, unsigned long long &cnt_out, double &sum_out);
+
+// Sets of at most 32 objects on a one-warp-per-set band are counted by the prepare kernel
+// itself, by the warp that has just reduced them (their objects are in its lanes' cache
+// lines): they get no work item, and their count and sum go to dcnt / dsum.
 __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, SetAux *aux,
-                            const BandTable *bt, int32_t *cnt, uint32_t *flags, BatchState *st) {
+                            const BandTable *bt, int32_t *cnt, uint32_t *flags, BatchState *st,
+                            unsigned long long *dcnt, double *dsum) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -270,10 +277,29 @@ __global__ void k_b_prepare(const BatchParams *__restrict__ P, SetDesc *sets, Se
         } else if (d.dtype == CC_I32) {
             x.mode = MODE_I32_WIDE;
         }
+        const Band &bb = band_of(*bt, d.n);
+        const bool direct = flag == SET_OK && bb.r == 0 && d.n >= 2 && d.n <= 32;   // warp-uniform
+        unsigned long long dc = 0;
+        double ds = 0.0;
+        if (direct) {
+            const bool sum = P->want_sum != 0;
+            if (x.mode == MODE_I32_FAST) {
+                if (sum) run_tiny<MODE_I32_FAST, true>(d, x, dc, ds);
+                else run_tiny<MODE_I32_FAST, false>(d, x, dc, ds);
+            } else if (x.mode == MODE_F32) {
+                if (sum) run_tiny<MODE_F32, true>(d, x, dc, ds);
+                else run_tiny<MODE_F32, false>(d, x, dc, ds);
+            } else {
+                if (sum) run_tiny<MODE_I32_WIDE, true>(d, x, dc, ds);
+                else run_tiny<MODE_I32_WIDE, false>(d, x, dc, ds);
+            }
+        }
         if (lane == 0) {
             aux[k] = x;
+            dcnt[k] = dc;
+            dsum[k] = ds;
             const int64_t it =
-                flag == SET_OK ? items_of<int32_t>(band_of(*bt, d.n), static_cast<int32_t>(d.n)) : 0;
+                flag == SET_OK && !direct ? items_of<int32_t>(bb, static_cast<int32_t>(d.n)) : 0;
             cnt[k] = static_cast<int32_t>(it < 0x7FFFFFFF ? it : 0x7FFFFFFF);
             flags[k] = flag;
         }
@@ -606,7 +632,8 @@ __global__ void __launch_bounds__(kMainWarps * 32, MINB) k_b_main(const BatchPar
 
 __global__ void k_b_finish(const BatchParams *__restrict__ P, const int32_t *cnt, const int64_t *start,
                            const int64_t *bsum, const uint32_t *flags, const BatchState *st,
-                           const unsigned long long *pcnt, const double *psum) {
+                           const unsigned long long *pcnt, const double *psum,
+                           const unsigned long long *dcnt, const double *dsum) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -628,6 +655,8 @@ __global__ void k_b_finish(const BatchParams *__restrict__ P, const int32_t *cnt
             }
         }
         if (lane == 0) {
+            tc += dcnt[k];   // sets counted by the prepare kernel (0 for the others)
+            if (want_sum) ts += dsum[k];
             const bool bad = overflow || flags[k] != SET_OK;
             P->d_counts[k] = bad ? CC_COUNT_INVALID : tc;
             if (want_sum && P->d_sums) P->d_sums[k] = bad ? __int_as_float(0x7fc00000) : static_cast<float>(ts);
@@ -728,6 +757,8 @@ struct cc_plan {
     SetAux *d_aux = nullptr;
     int32_t *d_cnt = nullptr;
     uint32_t *d_flags = nullptr;
+    unsigned long long *d_dcnt = nullptr;   // per set: count made by the prepare kernel
+    double *d_dsum = nullptr;
     int64_t *d_start = nullptr;
     int64_t *d_bsum = nullptr;
     Item *d_items = nullptr;
@@ -750,7 +781,7 @@ static const void *main_kernel() { return reinterpret_cast<const void *>(k_b_mai
 static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
     const int sms = sm_count();
     k_b_prepare<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_sets, P->d_aux, P->d_bands, P->d_cnt, P->d_flags,
-                                        P->d_state);
+                                        P->d_state, P->d_dcnt, P->d_dsum);
     k_b_scan1<<<P->scan_blocks, kScanBlock, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum);
     k_b_scan2<<<1, kScanBlock, 0, s>>>(P->d_bsum, P->scan_blocks, P->d_state, P->item_cap);
     k_b_emit<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_items, P->d_state);
@@ -760,7 +791,7 @@ static cc_status plan_enqueue(cc_plan *P, cudaStream_t s) {
         CC_CUDA(cudaLaunchKernel(P->main_fn, dim3(P->main_grid), dim3(kMainWarps * 32), args, 0, s));
     }
     k_b_finish<<<sms * 8, 256, 0, s>>>(P->d_params, P->d_cnt, P->d_start, P->d_bsum, P->d_flags, P->d_state,
-                                       P->d_pcnt, P->d_psum);
+                                       P->d_pcnt, P->d_psum, P->d_dcnt, P->d_dsum);
     CC_CUDA(cudaGetLastError());
     return CC_OK;
 }
@@ -836,6 +867,8 @@ cc_status cc_plan_create(cc_plan **plan, const char *tune_table_json, int32_t ma
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_aux), sizeof(SetAux) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_cnt), sizeof(int32_t) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_flags), sizeof(uint32_t) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_dcnt), sizeof(unsigned long long) * max_sets);
+    e = e ? e : alloc(reinterpret_cast<void **>(&P->d_dsum), sizeof(double) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_start), sizeof(int64_t) * max_sets);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_bsum), sizeof(int64_t) * P->scan_blocks);
     e = e ? e : alloc(reinterpret_cast<void **>(&P->d_items), sizeof(Item) * P->item_cap);
@@ -861,8 +894,8 @@ void cc_plan_destroy(cc_plan *P) {
     if (!P) return;
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
-    void *bufs[] = {P->d_params, P->d_bands, P->d_sets, P->d_aux, P->d_cnt, P->d_flags, P->d_start,
-                    P->d_bsum, P->d_items, P->d_pcnt, P->d_psum, P->d_state};
+    void *bufs[] = {P->d_params, P->d_bands, P->d_sets, P->d_aux, P->d_cnt, P->d_flags, P->d_dcnt,
+                    P->d_dsum, P->d_start, P->d_bsum, P->d_items, P->d_pcnt, P->d_psum, P->d_state};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete P;
